@@ -1,0 +1,395 @@
+"""Pins for the CPU oracle: each test checks it against something other than
+itself -- the paper's worked example, closed forms, a textbook algorithm for
+d = 2, published generator outputs, brute force on tiny inputs, statistical
+expectations and invariants the paper proves (Prop. 1, Prop. 2).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2411_14968_gb300 import datagen
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _staircase_2d(x):
+    """Textbook 2-D skyline (minimisation), independent of Def. 1 code: sort by
+    (x, y); walk groups of equal x; inside a group only the points at the
+    group's minimum y can survive, and they survive iff that minimum is below
+    every y seen at strictly smaller x."""
+    n = x.shape[0]
+    order = np.lexsort((x[:, 1], x[:, 0]))
+    keep = np.zeros(n, bool)
+    best = math.inf
+    i = 0
+    while i < n:
+        j = i
+        while j < n and x[order[j], 0] == x[order[i], 0]:
+            j += 1
+        grp = order[i:j]
+        ymin = x[grp, 1].min()
+        if ymin < best:
+            keep[grp[x[grp, 1] == ymin]] = True
+        best = min(best, ymin)
+        i = j
+    return keep
+
+
+def _expected_maxima(n, d):
+    """E|Sky| of n i.i.d. continuous points in d dimensions (Bentley, Kung,
+    Schkolnick & Thompson 1978): A(n,1) = 1, A(n,d) = A(n-1,d) + A(n,d-1)/n."""
+    a = [1.0] * (n + 1)  # A(k, 1)
+    for _ in range(2, d + 1):
+        b = [0.0] * (n + 1)
+        for k in range(1, n + 1):
+            b[k] = b[k - 1] + a[k] / k
+        a = b
+    return a[n]
+
+
+# ---------------------------------------------------------------- Def. 1
+
+
+def test_dominance_truth_table(oracle_mod):
+    dom = oracle_mod.dominates
+    assert dom([1, 2], [1, 3])
+    assert dom([0, 0, 0], [0, 0, 1])
+    assert not dom([1, 2], [1, 2])          # duplicates never dominate
+    assert not dom([1, 3], [2, 2])          # incomparable
+    assert not dom([1, 3], [1, 2])          # worse on one attribute
+    assert not dom([-0.0, 1.0], [0.0, 1.0])  # -0 == +0
+    assert dom([1, 1], [1, np.inf])
+    assert not dom([np.inf], [np.inf])
+    assert dom([-1.0, 5.0], [0.0, 5.0])     # negatives compare as reals
+
+
+def test_example1_cars(oracle_mod):
+    names, rows = [], []
+    with open(os.path.join(GOLDEN, "example1_cars.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            n, a, b = line.split()
+            names.append(n)
+            rows.append((float(a), float(b)))
+    pts = np.array(rows, np.float32)
+    sky = {names[i] for i in np.nonzero(oracle_mod.skyline_brute(pts))[0]}
+    assert sky == {"C1", "C2", "C4"}
+    assert set(names[i] for i in oracle_mod.skyline_indices(pts)) == sky
+    c = {nm: pts[i] for i, nm in enumerate(names)}
+    assert oracle_mod.dominates(c["C4"], c["C3"]) and oracle_mod.dominates(c["C4"], c["C5"])
+    # top-1 of monotone functions is in the skyline (Section 2)
+    assert names[int(np.argmin(pts[:, 0]))] == "C1"
+    assert names[int(np.argmin(pts[:, 1]))] == "C4"
+    assert names[int(np.argmin(pts.sum(1)))] == "C2"
+
+
+def test_d1_closed_form(oracle_mod):
+    rng = np.random.default_rng(5)
+    for n in (1, 2, 17, 1000):
+        x = rng.integers(0, 7, size=(n, 1)).astype(np.float32)
+        want = np.nonzero(x[:, 0] == x[:, 0].min())[0]
+        np.testing.assert_array_equal(oracle_mod.skyline_indices(x), want)
+        np.testing.assert_array_equal(np.nonzero(oracle_mod.skyline_brute(x))[0], want)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("n,levels", [(50, 8), (3000, 64), (200000, 0)])
+def test_d2_staircase(oracle_mod, seed, n, levels):
+    rng = np.random.default_rng(seed)
+    x = rng.random((n, 2))
+    if levels:
+        x = np.floor(x * levels) / levels  # many ties and duplicates
+    x = x.astype(np.float32)
+    want = np.nonzero(_staircase_2d(x))[0]
+    np.testing.assert_array_equal(oracle_mod.skyline_indices(x), want)
+    if n <= 3000:
+        np.testing.assert_array_equal(np.nonzero(oracle_mod.skyline_brute(x))[0], want)
+
+
+def test_perfectly_correlated(oracle_mod):
+    rng = np.random.default_rng(3)
+    t = rng.permutation(500).astype(np.float32)
+    x = np.repeat(t[:, None], 5, axis=1)
+    np.testing.assert_array_equal(oracle_mod.skyline_indices(x), [int(np.argmin(t))])
+
+
+def test_all_equal_points_all_in_skyline(oracle_mod):
+    x = np.full((64, 3), 0.25, np.float32)
+    np.testing.assert_array_equal(oracle_mod.skyline_indices(x), np.arange(64))
+
+
+def test_empty_and_single(oracle_mod):
+    assert oracle_mod.skyline_indices(np.zeros((0, 3), np.float32)).shape == (0,)
+    np.testing.assert_array_equal(oracle_mod.skyline_indices(np.ones((1, 4), np.float32)), [0])
+
+
+# --------------------------------------------------- Algorithm 1 (SFS)
+
+
+@pytest.mark.parametrize("kind", ["anticorrelated", "independent", "correlated", "skewed"])
+@pytest.mark.parametrize("d", [1, 2, 3, 5, 8])
+def test_sfs_equals_brute_force(oracle_mod, kind, d):
+    for seed in (1, 2):
+        x = datagen.make(kind, 1500, d, seed)
+        np.testing.assert_array_equal(oracle_mod.sfs(x)[0], oracle_mod.skyline_brute(x))
+
+
+def test_sfs_test_count_hand_case(oracle_mod):
+    # A=(1,1) f=2, B=(0,3) f=3, C=(2,2) f=4.  Window after A: {A}; B vs A: 1
+    # test, kept; C vs A: 1 test, dominated.  Two tests in all.
+    x = np.array([[2, 2], [0, 3], [1, 1]], np.float32)
+    mask, tests = oracle_mod.sfs(x)
+    assert mask.tolist() == [False, True, True]
+    assert tests == 2
+
+
+def test_score_is_left_to_right_fp32(oracle_mod):
+    # ((2^24 + 1) + 1) rounds to 2^24 at each step; the exact sum is 2^24 + 2.
+    x = np.array([[2.0 ** 24, 1.0, 1.0], [1.0, 1.0, 2.0 ** 24]], np.float32)
+    f = oracle_mod.scores(x)
+    assert f[0] == np.float32(2.0 ** 24)
+    assert f[1] == np.float32(2.0 ** 24 + 2)
+
+
+def test_expected_skyline_size_uniform(oracle_mod):
+    n = 20000
+    for d in (3, 4):
+        sizes = [int(oracle_mod.sfs(datagen.independent(n, d, s, quantised=False))[0].sum())
+                 for s in range(8)]
+        want = _expected_maxima(n, d)
+        assert abs(np.mean(sizes) - want) < 0.1 * want, (d, np.mean(sizes), want)
+
+
+# ------------------------------------------------------------ invariants
+
+
+def test_invariants_permutation_monotone_maps_duplicates(oracle_mod):
+    x = datagen.anticorrelated(2000, 4, 11)
+    base = set(oracle_mod.skyline_indices(x).tolist())
+    perm = np.random.default_rng(0).permutation(x.shape[0])
+    got = oracle_mod.skyline_indices(x[perm])
+    assert set(perm[got].tolist()) == base
+    # strictly increasing exact maps per column: x -> 2x and x -> dense rank
+    assert set(oracle_mod.skyline_indices(2 * x).tolist()) == base
+    ranks = np.empty_like(x)
+    for j in range(x.shape[1]):
+        _, inv = np.unique(x[:, j], return_inverse=True)
+        ranks[:, j] = inv.astype(np.float32)
+    assert set(oracle_mod.skyline_indices(ranks).tolist()) == base
+    # appending a copy of a skyline point adds the copy to the skyline
+    k = min(base)
+    y = np.vstack([x, x[k:k + 1]])
+    assert set(oracle_mod.skyline_indices(y).tolist()) == base | {x.shape[0]}
+
+
+def test_output_is_exact_skyline(oracle_mod):
+    """(I1) no output dominated by an output; (I2) every other point dominated
+    by some output point -- together equivalent to correctness."""
+    x = datagen.skewed(1200, 5, 4)
+    idx = oracle_mod.skyline_indices(x)
+    s = x[idx]
+    rest = np.setdiff1d(np.arange(x.shape[0]), idx)
+    assert oracle_mod.relative_skyline(s, s).all()
+    assert not oracle_mod.relative_skyline(x[rest], s).any()
+
+
+def test_relative_skyline(oracle_mod):
+    x = datagen.independent(500, 3, 9)
+    np.testing.assert_array_equal(oracle_mod.relative_skyline(x, x), oracle_mod.skyline_brute(x))
+    assert oracle_mod.relative_skyline(x, np.zeros((0, 3), np.float32)).all()
+    c = np.zeros((1, 3), np.float32)
+    r = np.array([[0, 0, 0], [0, 0, 1], [1, 1, 1]], np.float32)
+    assert oracle_mod.relative_skyline(r, c).tolist() == [True, False, False]
+
+
+# ------------------------------------------------------- partitioning
+
+
+def test_splitmix64_published_outputs(oracle_mod):
+    # first outputs of SplitMix64 started from state 0 (Steele, Lea & Flood 2014)
+    assert oracle_mod.splitmix64(0, 0) == 0xE220A8397B1DCDAF
+    assert oracle_mod.splitmix64(0, 1) == 0x6E789E6AA1B965F4
+    assert oracle_mod.splitmix64(0, 2) == 0x06C45D188009454F
+
+
+def test_grid_hand_values(oracle_mod):
+    x = np.array([[0.25, 0.75], [0.5, 0.0], [1.0, 1.0], [-3.0, 0.49], [0.0, np.inf]], np.float32)
+    # digits (0,1) (1,0) (1,1) (0,0) (0,1) with m = 2; index = c1 + 2 c2 (Section 3.2)
+    assert oracle_mod.assign_grid(x, [2, 2]).tolist() == [2, 1, 3, 0, 2]
+    # m = 3 and 4 per dimension: digits (0,3) (1,0) (2,3) (0,1) (0,3)
+    assert oracle_mod.assign_grid(x, [3, 4]).tolist() == [9, 1, 11, 3, 9]
+
+
+def test_grid_cells_are_dominance_consistent(oracle_mod):
+    x = datagen.independent(400, 3, 2)
+    pid = oracle_mod.assign_grid(x, [3, 3, 3])
+    c = np.stack([pid % 3, (pid // 3) % 3, pid // 9], 1)
+    # if c_i grid-dominates c_h then every tuple of c_i dominates every tuple of c_h
+    for i in range(0, 400, 7):
+        for h in range(400):
+            if np.all(c[i] < c[h]):
+                assert oracle_mod.dominates(x[i], x[h])
+
+
+def test_grid_filter_hand_and_soundness(oracle_mod):
+    m = [2, 2]
+    x = np.array([[0.1, 0.1], [0.9, 0.9], [0.8, 0.2]], np.float32)
+    pid = oracle_mod.assign_grid(x, m)
+    assert oracle_mod.grid_filter(pid, 2, m).tolist() == [False, False, False, True]
+    x2 = np.array([[0.1, 0.9], [0.9, 0.1]], np.float32)
+    assert not oracle_mod.grid_filter(oracle_mod.assign_grid(x2, m), 2, m).any()
+    for kind in ("independent", "correlated"):
+        x = datagen.make(kind, 3000, 3, 5)
+        pid = oracle_mod.assign_grid(x, [4, 4, 4])
+        dropped = oracle_mod.grid_filter(pid, 3, [4, 4, 4])
+        sky = oracle_mod.skyline_brute(x)
+        assert not np.any(sky & dropped[pid])
+        assert dropped.any()
+
+
+def test_angular_matches_atan2(oracle_mod):
+    rng = np.random.default_rng(8)
+    for d, m in ((2, [4]), (3, [5, 5]), (6, [4, 2, 2, 2, 2]), (4, [3, 7, 2])):
+        x = rng.random((5000, d)).astype(np.float32)
+        x[:50, 0] = 0.0
+        pid = oracle_mod.assign_angular(x, m)
+        xd = x.astype(np.float64)
+        w = 1
+        for i in range(d - 1):
+            phi = np.arctan2(np.sqrt((xd[:, i + 1:] ** 2).sum(1)), xd[:, i])
+            v = 2.0 * phi * m[i] / np.pi
+            want = np.minimum(np.floor(v), m[i] - 1).astype(np.int64)
+            got = (pid // w) % m[i]
+            near = np.abs(v - np.round(v)) < 1e-5
+            bad = (got != want) & ~near
+            assert not bad.any(), (d, i, np.nonzero(bad)[0][:5])
+            w *= m[i]
+        assert pid.max() < w
+
+
+def test_random_partitions_equinumerous(oracle_mod):
+    n, p = 10007, 16
+    a = oracle_mod.assign_random(n, p, 42)
+    cnt = np.bincount(a, minlength=p)
+    assert cnt.min() == n // p and cnt.max() == -(-n // p)
+    b = oracle_mod.assign_random(n, p, 43)
+    assert (a != b).mean() > 0.5
+    # not index order: the first 1/p of the indices spread over all partitions
+    assert len(np.unique(a[: n // p])) == p
+
+
+def test_sliced_sizes_and_dominance_order(oracle_mod):
+    x = datagen.anticorrelated(4000, 4, 3)
+    pid = oracle_mod.assign_sliced(x, 8)
+    cnt = np.bincount(pid, minlength=8)
+    assert cnt.max() - cnt.min() <= 1
+    order = np.argsort(x[:, 0], kind="stable")
+    assert np.all(np.diff(pid[order].astype(np.int64)) >= 0)
+    # quantised data: slice boundaries never split an equal-key run, so a
+    # dominator is never in a later slice (makes pd_i = {u_j : j < i} sound)
+    y = datagen.independent(600, 3, 1)
+    y = np.floor(y * 4) / 4
+    y = y.astype(np.float32)
+    q = oracle_mod.assign_sliced(y, 6)
+    for s in range(600):
+        for t in range(600):
+            if q[s] > q[t]:
+                assert not oracle_mod.dominates(y[s], y[t])
+
+
+# ------------------------------------------------ Algorithm 2 and Section 4
+
+SCHEMES = [
+    ("none", {"scheme": 4}),
+    ("random", {"scheme": 0, "p": 7, "seed": 99}),
+    ("grid", {"scheme": 1, "slices": None}),
+    ("angular", {"scheme": 2, "slices": None}),
+    ("sliced", {"scheme": 3, "p": 5}),
+]
+
+
+@pytest.mark.parametrize("kind", ["anticorrelated", "independent", "correlated", "skewed"])
+@pytest.mark.parametrize("d", [2, 3, 5, 8])
+def test_partitioned_equals_skyline(oracle_mod, kind, d):
+    """Prop. 1 (any partitioning) and Prop. 2 (NoSeq) with Grid Filtering and
+    Sorted representatives: every variant returns Sky(r)."""
+    x = datagen.make(kind, 700, d, d * 7 + 1)
+    want = np.nonzero(oracle_mod.skyline_brute(x))[0]
+    norm = kind == "skewed"
+    for name, kw in SCHEMES:
+        kw = dict(kw)
+        if name == "grid":
+            kw["slices"] = [2] * d if d > 3 else [3] * d
+        if name == "angular":
+            kw["slices"] = ([3, 2, 2, 2, 2, 2, 2][: d - 1]) if d > 1 else []
+        for rep in (0, 1):
+            for merge in (0, 1):
+                r = oracle_mod.partitioned(x, normalize=norm, rep=rep, merge=merge, **kw)
+                np.testing.assert_array_equal(r["indices"], want, err_msg=f"{name} rep={rep} merge={merge}")
+                st = r["stage"]
+                assert np.all((st >= 1) & (st <= 5))
+                # every point removed before the merge is dominated by some point
+                early = np.nonzero((st == 2) | (st == 3) | (st == 4))[0]
+                assert not oracle_mod.relative_skyline(x[early], x).any()
+                # points dropped inside a partition are dominated inside it
+                for i in np.nonzero(st == 4)[0][:50]:
+                    mates = x[r["pid"] == r["pid"][i]]
+                    assert not oracle_mod.relative_skyline(x[i:i + 1], mates)[0]
+
+
+def test_partitioned_edge_cases(oracle_mod):
+    for n in (0, 1, 2, 3):
+        x = datagen.independent(n, 3, 1)
+        want = np.nonzero(oracle_mod.skyline_brute(x))[0] if n else np.zeros(0, np.uint32)
+        for name, kw in SCHEMES:
+            kw = dict(kw)
+            if name == "grid":
+                kw["slices"] = [2, 2, 2]
+            if name == "angular":
+                kw["slices"] = [2, 2]
+            r = oracle_mod.partitioned(x, rep=1, merge=1, **kw)
+            np.testing.assert_array_equal(r["indices"], want)
+    # all points identical: every point is in the skyline
+    x = np.full((100, 4), 0.5, np.float32)
+    r = oracle_mod.partitioned(x, scheme=3, p=10, rep=1, merge=1)
+    np.testing.assert_array_equal(r["indices"], np.arange(100))
+
+
+def test_grid_filter_drops_in_pipeline(oracle_mod):
+    x = datagen.correlated(3000, 4, 2)
+    r = oracle_mod.partitioned(x, scheme=1, slices=[2, 2, 2, 2])
+    assert (r["stage"] == 2).sum() > 0
+
+
+# ------------------------------------------------------------- generators
+
+
+def test_generators_shapes_and_ranges():
+    a = datagen.anticorrelated(5000, 6, 1)
+    assert a.shape == (5000, 6) and a.dtype == np.float32
+    assert a.min() >= 0 and a.max() <= 1
+    s = a.astype(np.float64).sum(1) / 6
+    # rejection outside [0,1]^d favours smaller plane offsets, so the median
+    # sits a little below the drawn mean of 0.5
+    assert 0.44 < np.median(s) < 0.51 and 0.02 < s.std() < 0.07
+    q = datagen.independent(5000, 8, 1)
+    assert np.all(q * 256 == np.rint(q * 256))
+    c = datagen.correlated(5000, 8, 1)
+    assert np.corrcoef(c[:, 0], c[:, 1])[0, 1] > 0.9
+    k = datagen.skewed(20000, 6, 1)
+    assert k.min() > 0
+    _, counts = np.unique(k, axis=0, return_counts=True)
+    assert (counts > 1).sum() > 0.05 * 20000 / 2
+    assert np.all((k == k.max(0)).mean(0) > 0.03)
+    np.testing.assert_array_equal(datagen.anticorrelated(100, 3, 7), datagen.anticorrelated(100, 3, 7))
+
+
+def test_key_scale_column_max(oracle_mod):
+    x = np.array([[0.5, -2.0, 3.0], [4.0, -1.0, np.inf]], np.float32)
+    # positive finite column maxima scale the key; otherwise the scale is 1
+    assert oracle_mod.key_scale(x).tolist() == [4.0, 1.0, 1.0]
+    g = oracle_mod.assign_grid(np.array([[2.0, 0.0, 0.0]], np.float32), [2, 2, 2], normalize=False)
+    assert g.tolist() == [1]
