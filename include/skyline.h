@@ -1,0 +1,161 @@
+/*
+ * skyline.h -- C ABI of libskyline, a GB300 (sm_103a) implementation of the
+ * partitioned skyline method of Ciaccia & Martinenghi, "Optimization
+ * Strategies for Parallel Computation of Skylines" (arXiv 2411.14968).
+ *
+ * Problem (Section 2, Def. 1): given a relation r of N tuples with d numeric
+ * attributes, all to be minimised, a tuple t dominates s (t < s) iff
+ * t[A] <= s[A] for every attribute A and t[A'] < s[A'] for at least one A'.
+ * The skyline Sky(r) is the set of tuples that no tuple of r dominates.  Exact
+ * duplicates never dominate each other, so every copy of a skyline tuple is
+ * returned.  Comparisons are exact IEEE FP32 comparisons (no reduced
+ * precision, no flush-to-zero); -0.0 equals +0.0; +-inf are allowed; NaN is
+ * rejected.
+ *
+ * Method (Algorithm 2, Section 3): Partition r into r_1..r_p (Random 3.1,
+ * Grid 3.2, Angular 3.3, Sliced 3.4), optionally drop grid-dominated cells
+ * (Grid Filtering, 3.2) and tuples dominated by representatives (4.1),
+ * compute every local skyline u_i = Sky(r_i) with the sort-filter-skyline
+ * order of Algorithm 1, then merge: Sky(u) over u = union of u_i (sequential
+ * final phase) or the NoSeq identity Sky(r) = union_i Sky_{pd_i}(u_i)
+ * (Section 4.2, Prop. 2).  Every variant returns the same set (Prop. 1,
+ * Prop. 2), so the result never depends on the parameters.
+ *
+ * Conventions of every call:
+ *  - status codes are returned; nothing is thrown across the ABI;
+ *  - `points` is row-major N x d FP32, caller-owned and read-only; it may be
+ *    host memory (pageable or pinned) or device memory of the context's
+ *    device -- the library asks the CUDA runtime which;
+ *  - index outputs are caller-owned u32 arrays of capacity >= N in host or
+ *    device memory (again detected); indices are 0-based and ascending;
+ *  - a context owns its device scratch memory, grows it on demand within
+ *    its memory budget and frees it in sky_destroy;
+ *  - calls on one context must not run concurrently from several host
+ *    threads.
+ */
+#ifndef SKYLINE_H_
+#define SKYLINE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SKY_OK = 0,
+  SKY_EINVAL = 1,     /* bad argument: d outside 1..8, N >= 2^32, NaN, bad params */
+  SKY_ENOMEM = 2,     /* scratch memory beyond the context budget or cudaMalloc failed */
+  SKY_ECUDA = 3,      /* a CUDA runtime call failed; sky_last_error says which */
+  SKY_ETIMEOUT = 4,   /* a bounded device-side wait gave up (the GPU stays usable) */
+  SKY_EBUSY = 5,      /* a ticket is still in flight (sky_poll) */
+  SKY_ECANCELLED = 6  /* unknown or already collected ticket */
+} sky_status;
+
+typedef enum {
+  SKY_RANDOM = 0,   /* Section 3.1: random, equi-numerous partitions */
+  SKY_GRID = 1,     /* Section 3.2: m_i slices per attribute, p = prod m_i cells */
+  SKY_ANGULAR = 2,  /* Section 3.3: m_i slices per hyperspherical angle (d-1 angles) */
+  SKY_SLICED = 3,   /* Section 3.4: p equal slices along one attribute */
+  SKY_NONE = 4      /* one partition: plain SFS (Algorithm 1) over the whole input */
+} sky_partitioning;
+
+typedef enum { SKY_REP_NONE = 0, SKY_REP_SORTED = 1 } sky_rep;
+typedef enum { SKY_MERGE_SEQUENTIAL = 0, SKY_MERGE_NOSEQ = 1 } sky_merge;
+typedef enum {
+  SKY_EXEC_PERSISTENT = 0, /* all partitions' local skylines in one cooperative launch */
+  SKY_EXEC_PLAIN = 1       /* one launch per partition, in partition order */
+} sky_exec;
+
+typedef struct {
+  uint32_t struct_size;        /* sizeof(sky_params); filled by sky_params_init */
+  sky_partitioning scheme;
+  uint32_t num_partitions;     /* Random / Sliced: p (clamped to [1, N]) */
+  uint32_t slices[8];          /* Grid: m per attribute (d used); Angular: m per angle (d-1 used) */
+  uint32_t normalize;          /* Grid / Angular: divide each attribute by its column maximum
+                                  for the partition key only (dominance uses raw values) */
+  uint32_t slice_dim;          /* Sliced: attribute to slice on (default 0) */
+  uint64_t seed;               /* Random: SplitMix64 seed */
+  uint32_t grid_filter;        /* Grid: drop cells a non-empty cell grid-dominates (default 1) */
+  sky_rep rep;                 /* representative filtering (Section 4.1) */
+  uint32_t reps_per_partition; /* Sorted representatives per partition (default 1) */
+  sky_merge merge;             /* final phase (Section 4.2) */
+  sky_exec exec;               /* launch form of the local-skyline phase */
+  /* tuning knobs of the dominance engine; 0 selects the built-in default */
+  uint32_t chunk_min;          /* smallest SFS chunk of a partition (points) */
+  uint32_t chunk_max;          /* largest SFS chunk of a partition (points) */
+  uint32_t chunk_alpha_x4;     /* next chunk = alpha/4 x current window size, clamped */
+  uint32_t dom_block;          /* dominator block per work item (points, multiple of 32) */
+} sky_params;
+
+/* Per-call statistics (the last sky_skyline call of the context). */
+typedef struct {
+  uint64_t n;                  /* input points */
+  uint32_t d;
+  uint32_t partitions;         /* p after clamping */
+  uint32_t nonempty_partitions;
+  uint32_t rounds_local;       /* SFS rounds of the local phase (max over partitions) */
+  uint32_t rounds_merge;       /* SFS rounds of the sequential merge */
+  uint32_t reps_kept;          /* representatives left after removing dominated ones */
+  uint64_t grid_dropped;       /* points in cells removed by Grid Filtering */
+  uint64_t rep_dropped;        /* points removed by representatives */
+  uint64_t local_union;        /* |u| = sum of local skyline sizes */
+  uint64_t skyline;            /* |Sky(r)| */
+  double ms_total;             /* device time of the whole call (0 unless timing is on) */
+  double ms_phase[6];          /* prep+sort, filters, local, merge, output, host copies */
+} sky_stats;
+
+typedef struct sky_ctx sky_ctx;
+
+/* Fills *p with the defaults: SKY_NONE, p = 1, slices 1, grid_filter 1,
+   reps_per_partition 1, sequential merge, persistent launch. */
+void sky_params_init(sky_params* p);
+
+/* Creates a context on CUDA device `device` whose scratch memory may grow up
+   to mem_budget_bytes (0 = no limit but the device's).  The context starts
+   on the legacy default stream.  On failure *ctx is NULL. */
+sky_status sky_create(sky_ctx** ctx, int device, size_t mem_budget_bytes);
+
+/* Runs every later call of the context on `cuda_stream` (a cudaStream_t of
+   the context's device; NULL = legacy default stream).  The stream is not
+   owned by the context. */
+sky_status sky_set_stream(sky_ctx* ctx, void* cuda_stream);
+
+/* Turns per-phase CUDA-event timing of the statistics on (1) or off (0). */
+sky_status sky_set_timing(sky_ctx* ctx, int on);
+
+/* Sky(points) by Algorithm 2 with the given parameters (NULL = defaults).
+   points: N x d FP32 row-major (host or device).  out_idx: capacity >= N
+   (host or device); receives the |Sky| ascending indices.  *out_count
+   (host) receives |Sky|.  N = 0 returns SKY_OK with count 0.  Blocks until
+   the result is in out_idx. */
+sky_status sky_skyline(sky_ctx* ctx, const float* points, uint64_t n, uint32_t d,
+                       const sky_params* params, uint32_t* out_idx, uint64_t* out_count);
+
+/* sky_skyline plus per-point diagnostics in input order (each may be NULL;
+   host or device, capacity >= N):
+     out_pid[i]   partition of point i (Section 3 index formula of the scheme);
+     out_stage[i] where point i left the method: 1 in Sky(r), 2 in a cell
+                  removed by Grid Filtering, 3 dominated by a representative,
+                  4 dominated inside its partition, 5 in u but not in Sky(r). */
+sky_status sky_skyline_ex(sky_ctx* ctx, const float* points, uint64_t n, uint32_t d,
+                          const sky_params* params, uint32_t* out_idx, uint64_t* out_count,
+                          uint32_t* out_pid, uint8_t* out_stage);
+
+/* Statistics of the last completed call. */
+sky_status sky_get_stats(sky_ctx* ctx, sky_stats* out);
+
+/* Text of a status code (static storage). */
+const char* sky_status_str(sky_status s);
+
+/* Message of the last failing call of the context (static while the context lives). */
+const char* sky_last_error(sky_ctx* ctx);
+
+/* Frees the context and its device memory (synchronises its stream first). */
+void sky_destroy(sky_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SKYLINE_H_ */

@@ -1,0 +1,238 @@
+// Internal declarations shared by the translation units of libskyline.
+// Nothing here is part of the public C ABI (include/skyline.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <type_traits>
+
+namespace sky {
+
+typedef uint32_t u32;
+typedef uint64_t u64;
+typedef uint8_t u8;
+
+constexpr u32 FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------- numerics
+// Monotone unsigned image of a non-NaN FP32 value (a < b <=> fkey(a) <
+// fkey(b), given -0.0 was turned into +0.0).  Only sort keys use it;
+// dominance always compares the FP32 values themselves.
+__host__ __device__ inline u32 fkey(float x) {
+#ifdef __CUDA_ARCH__
+  u32 b = __float_as_uint(x);
+#else
+  u32 b;
+  __builtin_memcpy(&b, &x, 4);
+#endif
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__host__ __device__ inline float fkey_inv(u32 k) {
+  u32 b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float x;
+  __builtin_memcpy(&x, &b, 4);
+  return x;
+#endif
+}
+
+// Number of float4 per stored point: 1 for d <= 4, 2 for d <= 8.  Padding
+// attributes are +0.0 in every point, so they never decide a dominance test.
+__host__ __device__ constexpr int vec_of(int d) { return (d + 3) / 4; }
+
+// Bits of the device error word.
+enum : u32 {
+  ERR_NAN = 1u,       // an input attribute is NaN
+  ERR_TIMEOUT = 2u,   // a bounded wait gave up
+  ERR_CAPACITY = 4u,  // a device-side capacity check failed
+};
+
+// Partition schemes (same numbering as the public enum).
+enum : int { SCHEME_RANDOM = 0, SCHEME_GRID = 1, SCHEME_ANGULAR = 2, SCHEME_SLICED = 3, SCHEME_NONE = 4 };
+
+// Stage codes written per point (same numbering as the public documentation).
+enum : u8 { ST_SKY = 1, ST_GRID = 2, ST_REP = 3, ST_LOCAL = 4, ST_MERGE = 5 };
+
+template <class F>
+inline cudaError_t dispatch_d(int d, F&& f) {
+  switch (d) {
+    case 1: f(std::integral_constant<int, 1>()); break;
+    case 2: f(std::integral_constant<int, 2>()); break;
+    case 3: f(std::integral_constant<int, 3>()); break;
+    case 4: f(std::integral_constant<int, 4>()); break;
+    case 5: f(std::integral_constant<int, 5>()); break;
+    case 6: f(std::integral_constant<int, 6>()); break;
+    case 7: f(std::integral_constant<int, 7>()); break;
+    case 8: f(std::integral_constant<int, 8>()); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- primitives (sky_prims.cu)
+// Device-wide scan of n values (u8 or u32 input) into u32 (add or max).
+// tmp must hold scan_tmp_words(n) u32; tmp[scan_total_index(n)] receives the
+// total.  In-place (in == out) is allowed for u32.
+size_t scan_tmp_words(u64 n);
+u64 scan_total_index(u64 n);
+cudaError_t scan_u32(const u32* in, u32* out, u64 n, bool exclusive, bool use_max, u32* tmp,
+                     cudaStream_t st);
+cudaError_t scan_u8(const u8* in, u32* out, u64 n, bool exclusive, u32* tmp, cudaStream_t st);
+
+// Stable LSD radix sort of (u64 key, u32 value) pairs on key bits [lo_bit,
+// hi_bit).  Input in k[0], v[0]; *out_sel receives the index (0 or 1) of the
+// buffer pair that holds the output.  hist: radix_hist_words(n) u32; tmp:
+// scan_tmp_words(radix_hist_words(n)) u32.
+size_t radix_hist_words(u64 n);
+cudaError_t radix_sort(u64* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32* hist, u32* tmp,
+                       cudaStream_t st, int* out_sel);
+
+// ---------------------------------------------------------------- prep (sky_prep.cu)
+struct PrepArgs {
+  const float* X;        // row-major input, n x d
+  u64 n;
+  int scheme;
+  int normalize;         // divide attributes by the column maximum for keys
+  int slice_dim;
+  u64 seed;
+  u32 slices[8];
+  const u32* colmax;     // fkey of the column maxima (normalize only)
+  const float* ang_table;  // Angular thresholds tan^2(k pi / 2m), per angle
+  u32 ang_off[8];
+  u64* keys;             // out: first sort key
+  u32* vals;             // out: point index
+  u32* err;
+};
+
+struct GatherArgs {
+  const float* X;
+  u64 n;
+  const u64* keys;       // sorted keys; partition id in bits 63..32
+  const u32* vals;       // sorted point indices
+  u32 P;                 // partitions
+  float* pts;            // out: padded points in sorted order, vec_of(d) float4 each
+  float* score;          // out: scores in sorted order
+  u32* orig;             // out: original index of sorted position
+  u32* spid;             // out: partition of sorted position
+  u8* alive;             // out: 1
+  u32* seg_off;          // out: P + 1 segment offsets
+};
+
+cudaError_t launch_colmax(const float* X, u64 n, int d, u32* colmax, u32* err, cudaStream_t st);
+cudaError_t launch_prep(const PrepArgs& p, int d, cudaStream_t st);
+cudaError_t launch_rekey(const float* X, u64 n, int d, const u32* sorted_idx, const u32* run_start,
+                         u32 P, u64* keys, u32* vals, cudaStream_t st);
+cudaError_t launch_run_heads(const u64* keys, u64 n, u32* head, cudaStream_t st);
+cudaError_t launch_gather(const GatherArgs& g, int d, cudaStream_t st);
+
+struct GridDims { u32 m[8]; };
+cudaError_t launch_grid_filter(const u32* seg_off, const u32* spid, u64 n, int d, const GridDims& gd,
+                               u32 P, u8* clos, u8* dropped, u8* alive, u8* stage_s, u32* counter,
+                               cudaStream_t st);
+// Sorted representatives (4.1): the first k points of every non-empty,
+// non-dropped partition, packed; empty slots hold +inf points and
+// rep_alive 0.
+cudaError_t launch_rep_select(const u32* seg_off, u32 P, u32 k, const u8* dropped, const float* pts,
+                              int d, float* rep_pts, u8* rep_alive, cudaStream_t st);
+
+// Compaction of the points alive after the local phase into u (keeps the
+// (partition, score, index) order).
+cudaError_t launch_compact_u(const u8* alive, const u32* excl, u64 n, int d, const float* pts,
+                             const float* score, const u32* spid, float* upts, float* uscore,
+                             u32* upos, u32* upid, u64* ukey, u32* uval, cudaStream_t st);
+// useg[s] = offset of u_s in u (P + 1 entries); total = device pointer to |u|.
+cudaError_t launch_useg(const u32* seg_off, u32 P, const u32* excl, u64 n, const u32* total, u32* useg,
+                        cudaStream_t st);
+cudaError_t launch_gather_u(const u32* order, u64 n, int d, const float* upts, const float* uscore,
+                            const u32* upos, float* mpts, float* mscore, u32* mpos, cudaStream_t st);
+// Points dead in a merge array: their sorted-position flag is cleared and,
+// if no stage was recorded yet, stage `code` is recorded.
+cudaError_t launch_scatter_alive(const u8* malive, const u32* mpos, u64 n, u8* alive, u8* stage_s,
+                                 u8 code, cudaStream_t st);
+// Points dead (alive == 0) with no stage recorded get `code`.
+cudaError_t launch_stamp_stage(const u8* alive, u64 n, u8* stage_s, u8 code, cudaStream_t st);
+// Output mask in input order; a point with no stage recorded is in the
+// skyline (stage SKY).  Optional per-point diagnostics in input order.
+cudaError_t launch_output(u8* stage_s, const u32* orig, const u32* spid, u64 n, u8* mask,
+                          u8* stage_out, u32* pid_out, cudaStream_t st);
+cudaError_t launch_compact_idx(const u8* mask, const u32* excl, u64 n, u32* out, cudaStream_t st);
+cudaError_t launch_compact_reps(const u8* rep_alive, const u32* excl, u32 nrep, int d, const float* rep_pts,
+                                float* kept_pts, cudaStream_t st);
+cudaError_t launch_stage_hist(const u8* stage_s, u64 n, u32* hist6, cudaStream_t st);
+
+// ---------------------------------------------------------------- dominance engine (sky_dom.cu)
+// One segment (a partition, or the whole merge input) of the SFS engine.
+// The points of a segment are sorted by score; `win` has room for n points.
+struct SegDesc {
+  const float4* pts;     // vec_of(d) float4 per point, sorted by score
+  const float* score;
+  u8* alive;
+  float4* win;           // window: skyline points found so far (vec float4 per point)
+  u32* wpos;             // segment-relative position of each window point (may be null)
+  u32 n;
+  u32 d;                 // attributes (1..8)
+};
+
+// Round state of a segment (two copies, alternating by round parity).
+struct SegState {
+  u32 cur;          // first position of the current chunk
+  u32 cend;         // end of the current chunk (never splits a run of equal scores)
+  u32 wlen;         // window points visible to this round
+  u32 wfill;        // window append cursor (atomic)
+  u32 groups;       // candidate groups of the chunk
+  u32 items;        // work items of this round (groups x dominator blocks)
+  u32 done_groups;  // groups finished (atomic)
+  u32 rounds;       // rounds completed
+};
+
+struct EngineCfg {
+  u32 chunk_min, chunk_max, alpha_x4, dom_block;
+};
+
+struct EngineWork {
+  SegState* st;       // 2 * nseg
+  u32* done_round;    // nseg
+  u32* gdone;         // engine_group_capacity(...) counters, zero before the first launch
+  u64 gcap;
+  u32* ctl;           // ENGINE_CTL_WORDS control words
+};
+constexpr int ENGINE_CTL_WORDS = 16;
+u64 engine_group_capacity(u64 total_points, u32 nseg);
+
+// Local skylines of segs[0..nseg) in one cooperative launch (grid = the
+// co-resident capacity).  Kills dominated points (alive = 0) and leaves each
+// segment's skyline in its window.  ctl[5] receives the largest round count.
+cudaError_t engine_run(const SegDesc* segs_dev, u32 nseg, u32 max_vec, const EngineCfg& cfg,
+                       const EngineWork& w, u32* err, cudaStream_t st);
+cudaError_t launch_build_segs(const u32* seg_off, u32 P, const u8* dropped, const float* pts, const float* score,
+                              u8* alive, float* win, u32* wpos, int d, SegDesc* segs, cudaStream_t st);
+cudaError_t launch_build_one_seg(const float* pts, const float* score, u8* alive, float* win, const u32* n_dev,
+                                 int d, SegDesc* seg, cudaStream_t st);
+cudaError_t launch_fold_max(const u32* ctl, u32* dst, cudaStream_t st);
+
+// Relative skyline (Section 4.2 definition): kill every alive candidate of
+// cand[0..nc) dominated by one of dom[0..nd) (nd = *nd_dev if given, else
+// nd_host).
+cudaError_t launch_relative(const float* cand, u8* alive, u64 nc, const float* dom, u32 nd_host,
+                            const u32* nd_dev, int d, cudaStream_t st);
+
+// NoSeq final phase: u sorted by (partition, score) with offsets useg[P+1];
+// t in u_i is killed iff some s in pd_i dominates it.
+struct NoSeqArgs {
+  const float4* upts;
+  const float* uscore;
+  const u32* useg;   // P + 1
+  u8* ualive;
+  u32 P;
+  int scheme;
+  int d;
+  GridDims gd;       // Grid: slices per attribute
+  u32 dom_block;
+};
+cudaError_t launch_noseq(const NoSeqArgs& a, u32* gcnt, u32* gpre, u32* scan_tmp, const u32* nu_dev, u32* ctl,
+                         cudaStream_t st);
+
+int device_sm_count();
+
+}  // namespace sky

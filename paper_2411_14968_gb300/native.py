@@ -1,0 +1,255 @@
+"""ctypes binding of libskyline (include/skyline.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  There is no CPU fallback -- if the library cannot be loaded,
+every call raises.  Inputs may be numpy arrays (host memory; the library
+copies them to the GPU) or CUDA torch tensors (device memory, used in place
+on the tensor's current stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SKY_OK, SKY_EINVAL, SKY_ENOMEM, SKY_ECUDA, SKY_ETIMEOUT, SKY_EBUSY, SKY_ECANCELLED = range(7)
+SCHEMES = {"random": 0, "grid": 1, "angular": 2, "sliced": 3, "none": 4}
+REPS = {"none": 0, "sorted": 1}
+MERGES = {"sequential": 0, "noseq": 1}
+EXECS = {"persistent": 0, "plain": 1}
+STAGE_SKY, STAGE_GRID, STAGE_REP, STAGE_LOCAL, STAGE_MERGE = 1, 2, 3, 4, 5
+
+
+class SkyParams(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("scheme", ctypes.c_int),
+        ("num_partitions", ctypes.c_uint32),
+        ("slices", ctypes.c_uint32 * 8),
+        ("normalize", ctypes.c_uint32),
+        ("slice_dim", ctypes.c_uint32),
+        ("seed", ctypes.c_uint64),
+        ("grid_filter", ctypes.c_uint32),
+        ("rep", ctypes.c_int),
+        ("reps_per_partition", ctypes.c_uint32),
+        ("merge", ctypes.c_int),
+        ("exec", ctypes.c_int),
+        ("chunk_min", ctypes.c_uint32),
+        ("chunk_max", ctypes.c_uint32),
+        ("chunk_alpha_x4", ctypes.c_uint32),
+        ("dom_block", ctypes.c_uint32),
+    ]
+
+
+class SkyStats(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint64),
+        ("d", ctypes.c_uint32),
+        ("partitions", ctypes.c_uint32),
+        ("nonempty_partitions", ctypes.c_uint32),
+        ("rounds_local", ctypes.c_uint32),
+        ("rounds_merge", ctypes.c_uint32),
+        ("reps_kept", ctypes.c_uint32),
+        ("grid_dropped", ctypes.c_uint64),
+        ("rep_dropped", ctypes.c_uint64),
+        ("local_union", ctypes.c_uint64),
+        ("skyline", ctypes.c_uint64),
+        ("ms_total", ctypes.c_double),
+        ("ms_phase", ctypes.c_double * 6),
+    ]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "ms_phase"}
+        d["ms_phase"] = list(self.ms_phase)
+        return d
+
+
+EXPORTS = ["sky_params_init", "sky_create", "sky_set_stream", "sky_set_timing", "sky_skyline",
+           "sky_skyline_ex", "sky_get_stats", "sky_status_str", "sky_last_error", "sky_destroy"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SkylineError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Loads libskyline.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_missing else _build.LIB_PATH
+        if not os.path.exists(path):
+            raise RuntimeError(f"libskyline is not built ({path}); run build() first")
+        L = ctypes.CDLL(path)
+        P, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+        L.sky_params_init.argtypes = [ctypes.POINTER(SkyParams)]
+        L.sky_params_init.restype = None
+        L.sky_create.argtypes = [ctypes.POINTER(P), i32, ctypes.c_size_t]
+        L.sky_create.restype = i32
+        L.sky_set_stream.argtypes = [P, P]
+        L.sky_set_stream.restype = i32
+        L.sky_set_timing.argtypes = [P, i32]
+        L.sky_set_timing.restype = i32
+        L.sky_skyline.argtypes = [P, P, u64, u32, ctypes.POINTER(SkyParams), P, ctypes.POINTER(u64)]
+        L.sky_skyline.restype = i32
+        L.sky_skyline_ex.argtypes = [P, P, u64, u32, ctypes.POINTER(SkyParams), P, ctypes.POINTER(u64), P, P]
+        L.sky_skyline_ex.restype = i32
+        L.sky_get_stats.argtypes = [P, ctypes.POINTER(SkyStats)]
+        L.sky_get_stats.restype = i32
+        L.sky_status_str.argtypes = [i32]
+        L.sky_status_str.restype = ctypes.c_char_p
+        L.sky_last_error.argtypes = [P]
+        L.sky_last_error.restype = ctypes.c_char_p
+        L.sky_destroy.argtypes = [P]
+        L.sky_destroy.restype = None
+        _lib = L
+        return L
+
+
+def make_params(scheme="none", p: int = 1, slices=None, normalize=False, slice_dim=0, seed=0,
+                grid_filter=True, rep="none", reps_per_partition=1, merge="sequential",
+                exec="persistent", chunk_min=0, chunk_max=0, chunk_alpha_x4=0, dom_block=0) -> SkyParams:
+    L = load()
+    sp = SkyParams()
+    L.sky_params_init(ctypes.byref(sp))
+    sp.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    sp.num_partitions = int(p)
+    if slices is not None:
+        for i, m in enumerate(slices):
+            sp.slices[i] = int(m)
+    sp.normalize = int(bool(normalize))
+    sp.slice_dim = int(slice_dim)
+    sp.seed = int(seed) & (2 ** 64 - 1)
+    sp.grid_filter = int(bool(grid_filter))
+    sp.rep = REPS[rep] if isinstance(rep, str) else int(rep)
+    sp.reps_per_partition = int(reps_per_partition)
+    sp.merge = MERGES[merge] if isinstance(merge, str) else int(merge)
+    sp.exec = EXECS[exec] if isinstance(exec, str) else int(exec)
+    sp.chunk_min, sp.chunk_max = int(chunk_min), int(chunk_max)
+    sp.chunk_alpha_x4, sp.dom_block = int(chunk_alpha_x4), int(dom_block)
+    return sp
+
+
+def _is_cuda_tensor(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+class Context:
+    """One libskyline context on a CUDA device (owns its scratch memory)."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        self._L = load()
+        h = ctypes.c_void_p()
+        st = self._L.sky_create(ctypes.byref(h), int(device), int(mem_budget_bytes))
+        if st != SKY_OK:
+            raise SkylineError(st, self._L.sky_status_str(st).decode())
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.sky_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st):
+        if st != SKY_OK:
+            raise SkylineError(st, self._L.sky_last_error(self._h).decode())
+
+    def set_stream(self, stream_handle: int):
+        self._check(self._L.sky_set_stream(self._h, ctypes.c_void_p(int(stream_handle))))
+
+    def set_timing(self, on: bool):
+        self._check(self._L.sky_set_timing(self._h, int(bool(on))))
+
+    def stats(self) -> dict:
+        s = SkyStats()
+        self._check(self._L.sky_get_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def skyline(self, points, params: SkyParams | None = None, out=None, with_diag: bool = False, **kw):
+        """Sky(points): ascending indices of the non-dominated points.
+
+        points: numpy float32 [N, d] (host) or a CUDA torch float32 tensor.
+        Host input returns a numpy uint32 array; device input returns a CUDA
+        torch int32 tensor (a view of `out` if given).  with_diag also returns
+        the per-point partition and stage arrays (Section 3 / stage codes)."""
+        if params is None:
+            params = make_params(**kw)
+        elif kw:
+            raise TypeError("pass either params or keyword parameters")
+        cnt = ctypes.c_uint64(0)
+        if _is_cuda_tensor(points):
+            import torch
+            if points.dtype != torch.float32 or points.dim() != 2:
+                raise ValueError("points must be a float32 [N, d] tensor")
+            points = points.contiguous()
+            n, d = points.shape
+            self.set_stream(torch.cuda.current_stream(points.device).cuda_stream)
+            if out is None:
+                out = torch.empty(max(n, 1), dtype=torch.int32, device=points.device)
+            pid = stage = None
+            if with_diag:
+                pid = torch.empty(max(n, 1), dtype=torch.int32, device=points.device)
+                stage = torch.empty(max(n, 1), dtype=torch.uint8, device=points.device)
+            st = self._L.sky_skyline_ex(self._h, ctypes.c_void_p(points.data_ptr()), n, d, ctypes.byref(params),
+                                        ctypes.c_void_p(out.data_ptr()), ctypes.byref(cnt),
+                                        ctypes.c_void_p(pid.data_ptr()) if with_diag else None,
+                                        ctypes.c_void_p(stage.data_ptr()) if with_diag else None)
+            self._check(st)
+            res = out[: cnt.value]
+            if with_diag:
+                return res, pid[:n], stage[:n]
+            return res
+        a = np.ascontiguousarray(points, dtype=np.float32)
+        if a.ndim != 2:
+            raise ValueError("points must be [N, d]")
+        n, d = a.shape
+        self.set_stream(0)
+        res = np.zeros(max(n, 1), dtype=np.uint32)
+        pid = np.zeros(max(n, 1), dtype=np.uint32) if with_diag else None
+        stage = np.zeros(max(n, 1), dtype=np.uint8) if with_diag else None
+        st = self._L.sky_skyline_ex(self._h, a.ctypes.data_as(ctypes.c_void_p), n, d, ctypes.byref(params),
+                                    res.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt),
+                                    pid.ctypes.data_as(ctypes.c_void_p) if with_diag else None,
+                                    stage.ctypes.data_as(ctypes.c_void_p) if with_diag else None)
+        self._check(st)
+        if with_diag:
+            return res[: cnt.value], pid[:n], stage[:n]
+        return res[: cnt.value]
+
+
+_default_ctx = None
+
+
+def skyline(points, **kw):
+    """Sky(points) on CUDA device 0 with a process-wide default context."""
+    global _default_ctx
+    if _default_ctx is None:
+        _default_ctx = Context(0)
+    return _default_ctx.skyline(points, **kw)

@@ -1,0 +1,154 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Dominance is exact comparison arithmetic and the partition indices are
+integer or single-rounding FP32 definitions, so the bar is bit-exactness:
+the skyline index set, every point's partition and every point's stage code
+(where it left Algorithm 2) must equal the oracle's."""
+import numpy as np
+import pytest
+
+from paper_2411_14968_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2411_14968_gb300 import native
+    c = native.Context(0)
+    yield c
+    c.close()
+
+
+def _oracle_kw(scheme, p, slices, normalize, rep, merge, seed=0, slice_dim=0, grid_filter=True):
+    from oracle import oracle as O
+    return dict(scheme={"random": O.RANDOM, "grid": O.GRID, "angular": O.ANGULAR, "sliced": O.SLICED,
+                        "none": O.NONE}[scheme], p=p, slices=slices, normalize=normalize, seed=seed,
+                rep={"none": 0, "sorted": 1}[rep], merge={"sequential": 0, "noseq": 1}[merge],
+                slice_dim=slice_dim, grid_filter=grid_filter)
+
+
+def _check(ctx, oracle_mod, x, scheme="none", p=1, slices=None, normalize=False, rep="none",
+           merge="sequential", exec="persistent", seed=0, slice_dim=0, **tune):
+    want = oracle_mod.partitioned(x, **_oracle_kw(scheme, p, slices, normalize, rep, merge, seed, slice_dim))
+    idx, pid, stage = ctx.skyline(x, scheme=scheme, p=p, slices=slices, normalize=normalize, rep=rep,
+                                  merge=merge, exec=exec, seed=seed, slice_dim=slice_dim, with_diag=True, **tune)
+    tag = f"{scheme} p={p} slices={slices} rep={rep} merge={merge} exec={exec}"
+    np.testing.assert_array_equal(idx, want["indices"], err_msg=tag)
+    np.testing.assert_array_equal(pid, want["pid"], err_msg=tag + " pid")
+    np.testing.assert_array_equal(stage, want["stage"], err_msg=tag + " stage")
+    return idx
+
+
+# The tiny workload: N = 10,000 anticorrelated, d = 4, Grid m = 2 per dimension.
+def test_tiny_grid_anticorrelated(ctx, oracle_mod):
+    x = datagen.anticorrelated(10000, 4, 1)
+    for rep in ("none", "sorted"):
+        for merge in ("sequential", "noseq"):
+            for ex in ("persistent", "plain"):
+                _check(ctx, oracle_mod, x, "grid", slices=[2, 2, 2, 2], rep=rep, merge=merge, exec=ex)
+
+
+VARIANTS = [
+    ("none", 1, None),
+    ("random", 16, None),
+    ("sliced", 8, None),
+    ("grid", 1, "g"),
+    ("angular", 1, "a"),
+]
+
+
+@pytest.mark.parametrize("kind", ["anticorrelated", "independent", "correlated", "skewed"])
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_all_schemes(ctx, oracle_mod, kind, d):
+    x = datagen.make(kind, 3000, d, 100 + d)
+    norm = kind == "skewed"
+    for scheme, p, sl in VARIANTS:
+        slices = None
+        if sl == "g":
+            slices = [2] * d if d > 2 else [5] * d
+        elif sl == "a":
+            if d == 1:
+                continue
+            slices = ([4, 3, 2, 2, 2, 2, 2])[: d - 1]
+        for rep in ("none", "sorted"):
+            for merge in ("sequential", "noseq"):
+                _check(ctx, oracle_mod, x, scheme, p, slices, norm, rep, merge, seed=7)
+
+
+def test_multi_round_small_chunks(ctx, oracle_mod):
+    # small chunks and dominator blocks force many SFS rounds, many window
+    # blocks and ragged tails in every partition
+    x = datagen.anticorrelated(20000, 5, 3)
+    for scheme, p, sl in (("none", 1, None), ("sliced", 5, None), ("angular", 1, [3, 2, 2, 2])):
+        for ex in ("persistent", "plain"):
+            _check(ctx, oracle_mod, x, scheme, p, sl, exec=ex, chunk_min=96, chunk_max=700,
+                   chunk_alpha_x4=3, dom_block=64)
+
+
+def test_quantised_ties(ctx, oracle_mod):
+    # many equal scores and exact duplicates: chunk cuts must not split runs
+    for kind in ("independent", "correlated"):
+        x = datagen.make(kind, 30000, 8, 5)
+        x = (np.floor(x * 8) / 8).astype(np.float32)
+        for scheme, p, sl in (("none", 1, None), ("grid", 1, [2] * 8), ("random", 32, None)):
+            _check(ctx, oracle_mod, x, scheme, p, sl, rep="sorted", chunk_min=128, dom_block=96)
+
+
+def test_edge_values(ctx, oracle_mod):
+    rng = np.random.default_rng(4)
+    x = rng.random((4000, 3)).astype(np.float32)
+    x[:100] = 0.0
+    x[100:200] = -0.0
+    x[200:260, 1] = np.inf
+    x[260:300, 0] = -np.inf
+    x[300:340] = np.float32(1e-45)  # denormals: no flush to zero
+    x[340:380, 2] = np.float32(2e-45)
+    x[400:800] = x[800:1200]        # duplicates
+    for scheme, p, sl in VARIANTS:
+        slices = [3, 3, 3] if sl == "g" else ([3, 2] if sl == "a" else None)
+        _check(ctx, oracle_mod, x, scheme, p, slices, rep="sorted", merge="noseq")
+        _check(ctx, oracle_mod, x, scheme, p, slices, rep="none", merge="sequential")
+
+
+def test_small_n(ctx, oracle_mod):
+    for n in (1, 2, 3, 31, 32, 33, 63, 64, 65, 127, 129):
+        x = datagen.independent(n, 4, n)
+        for scheme, p, sl in VARIANTS:
+            slices = [2, 2, 2, 2] if sl == "g" else ([2, 2, 2] if sl == "a" else None)
+            _check(ctx, oracle_mod, x, scheme, p, slices, rep="sorted", merge="noseq")
+
+
+def test_empty_and_all_equal(ctx):
+    x = np.zeros((0, 5), np.float32)
+    assert ctx.skyline(x).shape == (0,)
+    y = np.full((5000, 6), 0.5, np.float32)
+    np.testing.assert_array_equal(ctx.skyline(y, scheme="sliced", p=7), np.arange(5000))
+
+
+def test_device_tensor_input(ctx, oracle_mod):
+    import torch
+    x = datagen.anticorrelated(50000, 6, 9)
+    want = oracle_mod.partitioned(x, scheme=oracle_mod.SLICED, p=16)["indices"]
+    t = torch.from_numpy(x).cuda()
+    got = ctx.skyline(t, scheme="sliced", p=16, rep="sorted")
+    assert got.is_cuda
+    np.testing.assert_array_equal(got.cpu().numpy().astype(np.uint32), want)
+
+
+def test_invalid_inputs(ctx):
+    from paper_2411_14968_gb300 import native
+    x = datagen.independent(100, 3, 1)
+    x[17, 1] = np.nan
+    with pytest.raises(native.SkylineError) as e:
+        ctx.skyline(x)
+    assert e.value.status == native.SKY_EINVAL
+    with pytest.raises(native.SkylineError):
+        ctx.skyline(np.zeros((10, 9), np.float32))
+    with pytest.raises(native.SkylineError):
+        ctx.skyline(datagen.independent(10, 3, 1), scheme="sliced", p=2, slice_dim=3)
+    # the context stays usable after errors
+    assert ctx.skyline(datagen.independent(100, 3, 1)).shape[0] > 0
