@@ -11,9 +11,17 @@
 #include <string>
 #include <vector>
 #include "../../include/skyline.h"
+#include "../../include/skyline_diag.h"
 #include "sky_internal.cuh"
 
 using namespace sky;
+
+namespace sky {
+u64& launch_counter() {
+  static thread_local u64 count = 0;
+  return count;
+}
+}  // namespace sky
 
 struct sky_ctx {
   int device = 0;
@@ -25,7 +33,7 @@ struct sky_ctx {
   u32* pinned = nullptr;  // small host staging area (pinned)
   std::string last_error;
   sky_stats stats;
-  cudaEvent_t ev[8] = {};
+  cudaEvent_t ev[12] = {};
 };
 
 namespace {
@@ -310,6 +318,7 @@ sky_status run(sky_ctx* ctx, const float* points, u64 n, u32 d, const sky_params
   Plan pl;
   sky_status s = validate(ctx, points, n, d, pa, &pl);
   if (s != SKY_OK) return s;
+  const u64 launches0 = launch_counter();
   if (!out_count) return fail(ctx, SKY_EINVAL, "out_count is NULL");
   CK(cudaSetDevice(ctx->device));
   memset(&ctx->stats, 0, sizeof(ctx->stats));
@@ -433,16 +442,17 @@ sky_status run(sky_ctx* ctx, const float* points, u64 n, u32 d, const sky_params
   ew.gdone = b.gdone;
   ew.gcap = b.gcap;
   ew.ctl = b.ctl;
-  if (P > 1 || true) {
-    if (pl.exec == SKY_EXEC_PERSISTENT) {
-      CK(engine_run(b.segs, P, pl.V, pl.cfg, ew, err, st));
+  record(ctx, 8);
+  if (pl.exec == SKY_EXEC_PERSISTENT) {
+    CK(engine_run(b.segs, P, pl.V, pl.cfg, ew, err, st));
+    record(ctx, 9);
+    CK(launch_fold_max(b.ctl, b.words + W_MAXROUND_LOCAL, st));
+  } else {
+    for (u32 q = 0; q < P; ++q) {
+      CK(engine_run(b.segs + q, 1, pl.V, pl.cfg, ew, err, st));
       CK(launch_fold_max(b.ctl, b.words + W_MAXROUND_LOCAL, st));
-    } else {
-      for (u32 q = 0; q < P; ++q) {
-        CK(engine_run(b.segs + q, 1, pl.V, pl.cfg, ew, err, st));
-        CK(launch_fold_max(b.ctl, b.words + W_MAXROUND_LOCAL, st));
-      }
     }
+    record(ctx, 9);
   }
   CK(launch_stamp_stage(b.alive, n, b.stage_s, ST_LOCAL, st));
   record(ctx, 4);
@@ -465,7 +475,9 @@ sky_status run(sky_ctx* ctx, const float* points, u64 n, u32 d, const sky_params
       CK(cudaMemsetAsync(b.malive, 1, nu ? nu : 1, st));
       CK(launch_build_one_seg(b.mpts, b.mscore, b.malive, b.win, b.words + W_NU, D, b.segs, st));
       CK(cudaMemsetAsync(b.gdone, 0, b.gcap * sizeof(u32), st));
+      record(ctx, 10);
       CK(engine_run(b.segs, 1, pl.V, pl.cfg, ew, err, st));
+      record(ctx, 11);
       CK(launch_fold_max(b.ctl, b.words + W_MAXROUND_MERGE, st));
       CK(launch_scatter_alive(b.malive, b.mpos, nu, b.alive, b.stage_s, ST_MERGE, st));
     } else {
@@ -483,7 +495,9 @@ sky_status run(sky_ctx* ctx, const float* points, u64 n, u32 d, const sky_params
       na.dom_block = pl.cfg.dom_block;
       // keep the item count within 32 bits
       while (((n / 64 + P + 1) * (n / na.dom_block + 1)) >= (1ull << 31)) na.dom_block *= 2;
+      record(ctx, 10);
       CK(launch_noseq(na, b.gcnt, b.gpre, b.scan_tmp, b.words + W_NU, b.ctl, st));
+      record(ctx, 11);
       // u is a prefix of the sorted positions' survivors: upos maps back
       CK(cudaMemcpyAsync(ctx->pinned, b.words + W_NU, sizeof(u32), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
@@ -532,15 +546,22 @@ sky_status run(sky_ctx* ctx, const float* points, u64 n, u32 d, const sky_params
   S.local_union = (u64)w[W_HIST + ST_MERGE] + w[W_HIST + ST_SKY];
   S.skyline = cnt;
   S.nonempty_partitions = 0;
+  S.launches = launch_counter() - launches0;
   if (ctx->timing) {
     float ms = 0;
     cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[7]);
     S.ms_total = ms;
-    const int edges[7] = {1, 2, 3, 4, 5, 6, 7};
     for (int i = 0; i < 6; ++i) {
       float t = 0;
-      cudaEventElapsedTime(&t, ctx->ev[edges[i]], ctx->ev[edges[i] + 1 <= 7 ? edges[i] + 1 : 7]);
+      cudaEventElapsedTime(&t, ctx->ev[i + 1], ctx->ev[i + 2]);
       S.ms_phase[i] = t;
+    }
+    float tl = 0, tm = 0;
+    cudaEventElapsedTime(&tl, ctx->ev[8], ctx->ev[9]);
+    S.ms_dom_local = tl;
+    if (P > 1) {
+      cudaEventElapsedTime(&tm, ctx->ev[10], ctx->ev[11]);
+      S.ms_dom_merge = tm;
     }
   }
   return SKY_OK;
@@ -580,7 +601,7 @@ sky_status sky_create(sky_ctx** ctx, int device, size_t mem_budget_bytes) {
     delete c;
     return SKY_ENOMEM;
   }
-  for (int i = 0; i < 8; ++i) cudaEventCreate(&c->ev[i]);
+  for (int i = 0; i < 12; ++i) cudaEventCreate(&c->ev[i]);
   device_sm_count();
   memset(&c->stats, 0, sizeof(c->stats));
   *ctx = c;
@@ -628,6 +649,16 @@ const char* sky_status_str(sky_status s) {
   return "unknown status";
 }
 
+sky_status sky_probe_compare_rate(sky_ctx* ctx, uint32_t iterations, double* compares_per_s,
+                                  uint32_t* sm_count) {
+  if (!ctx || !compares_per_s || !sm_count || iterations == 0) return SKY_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  sky_status s = ensure_ws(ctx, 256);
+  if (s != SKY_OK) return s;
+  CK(probe_compare_rate(iterations, ctx->stream, compares_per_s, sm_count, reinterpret_cast<u32*>(ctx->ws)));
+  return SKY_OK;
+}
+
 const char* sky_last_error(sky_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
 
 void sky_destroy(sky_ctx* ctx) {
@@ -636,7 +667,7 @@ void sky_destroy(sky_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 12; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   delete ctx;
 }

@@ -635,6 +635,7 @@ int g_sm_count = 0;
 cudaError_t launch_build_segs(const u32* seg_off, u32 P, const u8* dropped, const float* pts, const float* score,
                               u8* alive, float* win, u32* wpos, int d, SegDesc* segs, cudaStream_t st) {
   if (P == 0) return cudaSuccess;
+  note_launch();
   k_build_segs<<<(P + 255) / 256, 256, 0, st>>>(seg_off, P, dropped, reinterpret_cast<const float4*>(pts), score,
                                                 alive, reinterpret_cast<float4*>(win), wpos, d, segs);
   return cudaGetLastError();
@@ -642,12 +643,14 @@ cudaError_t launch_build_segs(const u32* seg_off, u32 P, const u8* dropped, cons
 
 cudaError_t launch_build_one_seg(const float* pts, const float* score, u8* alive, float* win, const u32* n_dev,
                                  int d, SegDesc* seg, cudaStream_t st) {
+  note_launch();
   k_build_one_seg<<<1, 1, 0, st>>>(reinterpret_cast<const float4*>(pts), score, alive,
                                    reinterpret_cast<float4*>(win), n_dev, d, seg);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fold_max(const u32* ctl, u32* dst, cudaStream_t st) {
+  note_launch();
   k_fold_max<<<1, 1, 0, st>>>(ctl + C_MAXROUND, dst);
   return cudaGetLastError();
 }
@@ -706,6 +709,7 @@ cudaError_t engine_run(const SegDesc* segs_dev, u32 nseg, u32 max_vec, const Eng
   attr[0].val.cooperative = 1;
   lc.attrs = attr;
   lc.numAttrs = 1;
+  note_launch();
   return cudaLaunchKernelEx(&lc, k_engine, P);
 }
 
@@ -715,6 +719,7 @@ cudaError_t launch_relative(const float* cand, u8* alive, u64 nc, const float* d
   u64 groups = (nc + GS - 1) / GS;
   unsigned grid = (unsigned)((groups + WARPS - 1) / WARPS);
   return dispatch_d(d, [&](auto D) {
+    note_launch();
     k_relative<decltype(D)::value><<<grid, THREADS, 0, st>>>(reinterpret_cast<const float4*>(cand), alive, nc,
                                                              reinterpret_cast<const float4*>(dom), nd_host, nd_dev);
   });
@@ -723,6 +728,7 @@ cudaError_t launch_relative(const float* cand, u8* alive, u64 nc, const float* d
 cudaError_t launch_noseq(const NoSeqArgs& a, u32* gcnt, u32* gpre, u32* scan_tmp, const u32* nu_dev, u32* ctl,
                          cudaStream_t st) {
   if (a.P == 0) return cudaSuccess;
+  note_launch();
   k_noseq_groups<<<(a.P + 255) / 256, 256, 0, st>>>(a.useg, a.P, gcnt);
   cudaError_t e = scan_u32(gcnt, gpre, a.P, true, false, scan_tmp, st);
   if (e != cudaSuccess) return e;
@@ -736,6 +742,7 @@ cudaError_t launch_noseq(const NoSeqArgs& a, u32* gcnt, u32* gpre, u32* scan_tmp
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_noseq<decltype(D)::value>, THREADS, 0);
     if (per_sm <= 0) per_sm = 1;
+    note_launch();
     k_noseq<decltype(D)::value><<<(unsigned)(sms * per_sm), THREADS, 0, st>>>(a, gpre, nu_dev, ctl);
   });
 }

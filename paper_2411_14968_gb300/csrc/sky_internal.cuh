@@ -54,6 +54,11 @@ enum : int { SCHEME_RANDOM = 0, SCHEME_GRID = 1, SCHEME_ANGULAR = 2, SCHEME_SLIC
 // Stage codes written per point (same numbering as the public documentation).
 enum : u8 { ST_SKY = 1, ST_GRID = 2, ST_REP = 3, ST_LOCAL = 4, ST_MERGE = 5 };
 
+// Kernel launches issued by this library in the calling host thread (each
+// launch site calls note_launch() right before its launch).
+u64& launch_counter();
+inline void note_launch() { ++launch_counter(); }
+
 template <class F>
 inline cudaError_t dispatch_d(int d, F&& f) {
   switch (d) {
@@ -234,5 +239,8 @@ cudaError_t launch_noseq(const NoSeqArgs& a, u32* gcnt, u32* gpre, u32* scan_tmp
                          cudaStream_t st);
 
 int device_sm_count();
+
+// Compare-throughput probe (sky_probe.cu).
+cudaError_t probe_compare_rate(u32 iters, cudaStream_t st, double* per_s, u32* sms_out, u32* sink);
 
 }  // namespace sky

@@ -422,14 +422,17 @@ __global__ void k_compact_idx(const u8* __restrict__ mask, const u32* __restrict
 }  // namespace
 
 cudaError_t launch_colmax(const float* X, u64 n, int d, u32* colmax, u32* err, cudaStream_t st) {
+  note_launch();
   k_colmax_init<<<1, 32, 0, st>>>(colmax);
   unsigned g = (unsigned)std::min<u64>((n + PT - 1) / PT, 4096);
   if (g == 0) return cudaGetLastError();
+  note_launch();
   return dispatch_d(d, [&](auto D) { k_colmax<decltype(D)::value><<<g, PT, 0, st>>>(X, n, colmax, err); });
 }
 
 cudaError_t launch_prep(const PrepArgs& p, int d, cudaStream_t st) {
   if (p.n == 0) return cudaSuccess;
+  note_launch();
   return dispatch_d(d, [&](auto D) { k_prep<decltype(D)::value><<<grid_for(p.n), PT, 0, st>>>(p); });
 }
 
@@ -437,33 +440,44 @@ cudaError_t launch_rekey(const float* X, u64 n, int d, const u32* sorted_idx, co
                          u32 P, u64* keys, u32* vals, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   return dispatch_d(d, [&](auto D) {
+    note_launch();
     k_rekey_rank<decltype(D)::value><<<grid_for(n), PT, 0, st>>>(X, n, sorted_idx, run_start, P, keys, vals);
   });
 }
 
 cudaError_t launch_run_heads(const u64* keys, u64 n, u32* head, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
+  note_launch();
   k_run_heads<<<grid_for(n), PT, 0, st>>>(keys, n, head);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather(const GatherArgs& g, int d, cudaStream_t st) {
   if (g.n == 0) return cudaSuccess;
+  note_launch();
   return dispatch_d(d, [&](auto D) { k_gather<decltype(D)::value><<<grid_for(g.n), PT, 0, st>>>(g); });
 }
 
 cudaError_t launch_grid_filter(const u32* seg_off, const u32* spid, u64 n, int d, const GridDims& gd,
                                u32 P, u8* clos, u8* dropped, u8* alive, u8* stage_s, u32* counter,
                                cudaStream_t st) {
+  note_launch();
   k_occupied<<<grid_for(P), PT, 0, st>>>(seg_off, P, clos);
   u32 stride = 1;
   for (int a = 0; a < d; ++a) {
     u64 nlines = P / gd.m[a];
-    if (nlines) k_closure_axis<<<grid_for(nlines), PT, 0, st>>>(clos, P, gd.m[a], stride);
+    if (nlines) {
+      note_launch();
+      k_closure_axis<<<grid_for(nlines), PT, 0, st>>>(clos, P, gd.m[a], stride);
+    }
     stride *= gd.m[a];
   }
+  note_launch();
   k_grid_dropped<<<grid_for(P), PT, 0, st>>>(clos, P, d, gd, dropped);
-  if (n) k_apply_dropped<<<grid_for(n), PT, 0, st>>>(spid, n, dropped, alive, stage_s, counter);
+  if (n) {
+    note_launch();
+    k_apply_dropped<<<grid_for(n), PT, 0, st>>>(spid, n, dropped, alive, stage_s, counter);
+  }
   return cudaGetLastError();
 }
 
@@ -472,6 +486,7 @@ cudaError_t launch_rep_select(const u32* seg_off, u32 P, u32 k, const u8* droppe
   u64 cnt = (u64)P * k;
   if (cnt == 0) return cudaSuccess;
   return dispatch_d(d, [&](auto D) {
+    note_launch();
     k_rep_select<decltype(D)::value><<<grid_for(cnt), PT, 0, st>>>(seg_off, P, k, dropped, pts, rep_pts, rep_alive);
   });
 }
@@ -480,6 +495,7 @@ cudaError_t launch_compact_reps(const u8* rep_alive, const u32* excl, u32 nrep, 
                                 float* kept_pts, cudaStream_t st) {
   if (nrep == 0) return cudaSuccess;
   return dispatch_d(d, [&](auto D) {
+    note_launch();
     k_compact_reps<decltype(D)::value><<<grid_for(nrep), PT, 0, st>>>(rep_alive, excl, nrep, rep_pts, kept_pts);
   });
 }
@@ -488,6 +504,7 @@ cudaError_t launch_stage_hist(const u8* stage_s, u64 n, u32* hist6, cudaStream_t
   cudaError_t e = cudaMemsetAsync(hist6, 0, 6 * sizeof(u32), st);
   if (e != cudaSuccess || n == 0) return e;
   unsigned g = (unsigned)std::min<u64>(grid_for(n), 1024);
+  note_launch();
   k_stage_hist<<<g, PT, 0, st>>>(stage_s, n, hist6);
   return cudaGetLastError();
 }
@@ -497,6 +514,7 @@ cudaError_t launch_compact_u(const u8* alive, const u32* excl, u64 n, int d, con
                              u32* upos, u32* upid, u64* ukey, u32* uval, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   return dispatch_d(d, [&](auto D) {
+    note_launch();
     k_compact_u<decltype(D)::value><<<grid_for(n), PT, 0, st>>>(alive, excl, n, pts, score, spid, upts,
                                                                uscore, upos, upid, ukey, uval);
   });
@@ -504,6 +522,7 @@ cudaError_t launch_compact_u(const u8* alive, const u32* excl, u64 n, int d, con
 
 cudaError_t launch_useg(const u32* seg_off, u32 P, const u32* excl, u64 n, const u32* total, u32* useg,
                         cudaStream_t st) {
+  note_launch();
   k_useg<<<grid_for((u64)P + 1), PT, 0, st>>>(seg_off, P, excl, n, total, useg);
   return cudaGetLastError();
 }
@@ -512,6 +531,7 @@ cudaError_t launch_gather_u(const u32* order, u64 n, int d, const float* upts, c
                             const u32* upos, float* mpts, float* mscore, u32* mpos, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   return dispatch_d(d, [&](auto D) {
+    note_launch();
     k_gather_u<decltype(D)::value><<<grid_for(n), PT, 0, st>>>(order, n, upts, uscore, upos, mpts, mscore,
                                                               mpos);
   });
@@ -520,12 +540,14 @@ cudaError_t launch_gather_u(const u32* order, u64 n, int d, const float* upts, c
 cudaError_t launch_scatter_alive(const u8* malive, const u32* mpos, u64 n, u8* alive, u8* stage_s,
                                  u8 code, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
+  note_launch();
   k_scatter_alive<<<grid_for(n), PT, 0, st>>>(malive, mpos, n, alive, stage_s, code);
   return cudaGetLastError();
 }
 
 cudaError_t launch_stamp_stage(const u8* alive, u64 n, u8* stage_s, u8 code, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
+  note_launch();
   k_stamp_stage<<<grid_for(n), PT, 0, st>>>(alive, n, stage_s, code);
   return cudaGetLastError();
 }
@@ -533,12 +555,14 @@ cudaError_t launch_stamp_stage(const u8* alive, u64 n, u8* stage_s, u8 code, cud
 cudaError_t launch_output(u8* stage_s, const u32* orig, const u32* spid, u64 n, u8* mask,
                           u8* stage_out, u32* pid_out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
+  note_launch();
   k_output<<<grid_for(n), PT, 0, st>>>(stage_s, orig, spid, n, mask, stage_out, pid_out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_compact_idx(const u8* mask, const u32* excl, u64 n, u32* out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
+  note_launch();
   k_compact_idx<<<grid_for(n), PT, 0, st>>>(mask, excl, n, out);
   return cudaGetLastError();
 }

@@ -125,8 +125,11 @@ cudaError_t scan_impl(const In* in, u32* out, u64 n, bool exclusive, u32* tmp, c
   if (nb == 0) {
     return cudaMemsetAsync(tmp, 0, sizeof(u32), st);
   }
+  note_launch();
   k_scan_reduce<In, Op><<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, tmp);
+  note_launch();
   k_scan_partials<Op><<<1, 1024, 0, st>>>(tmp, nb);
+  note_launch();
   k_scan_down<In, Op><<<(unsigned)nb, SCAN_T, 0, st>>>(in, out, n, tmp, exclusive);
   return cudaGetLastError();
 }
@@ -228,9 +231,11 @@ cudaError_t radix_sort(u64* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32*
   for (int shift = lo_bit; shift < hi_bit; shift += 8) {
     int bits = hi_bit - shift < 8 ? hi_bit - shift : 8;
     u32 mask = (1u << bits) - 1u;
+    note_launch();
     k_radix_hist<<<(unsigned)nb, RT, 0, st>>>(k[sel], n, shift, mask, hist, (u32)nb);
     cudaError_t e = scan_u32(hist, hist, (u64)RT * nb, true, false, tmp, st);
     if (e != cudaSuccess) return e;
+    note_launch();
     k_radix_scatter<<<(unsigned)nb, RT, 0, st>>>(k[sel], v[sel], k[sel ^ 1], v[sel ^ 1], n, shift,
                                                   mask, hist, (u32)nb);
     sel ^= 1;

@@ -60,6 +60,9 @@ class SkyStats(ctypes.Structure):
         ("skyline", ctypes.c_uint64),
         ("ms_total", ctypes.c_double),
         ("ms_phase", ctypes.c_double * 6),
+        ("launches", ctypes.c_uint64),
+        ("ms_dom_local", ctypes.c_double),
+        ("ms_dom_merge", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -69,7 +72,8 @@ class SkyStats(ctypes.Structure):
 
 
 EXPORTS = ["sky_params_init", "sky_create", "sky_set_stream", "sky_set_timing", "sky_skyline",
-           "sky_skyline_ex", "sky_get_stats", "sky_status_str", "sky_last_error", "sky_destroy"]
+           "sky_skyline_ex", "sky_get_stats", "sky_status_str", "sky_last_error", "sky_destroy",
+           "sky_probe_compare_rate"]
 
 _lock = threading.Lock()
 _lib = None
@@ -116,6 +120,8 @@ def load(build_if_missing: bool = True):
         L.sky_last_error.restype = ctypes.c_char_p
         L.sky_destroy.argtypes = [P]
         L.sky_destroy.restype = None
+        L.sky_probe_compare_rate.argtypes = [P, u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32)]
+        L.sky_probe_compare_rate.restype = i32
         _lib = L
         return L
 
@@ -186,6 +192,13 @@ class Context:
 
     def set_timing(self, on: bool):
         self._check(self._L.sky_set_timing(self._h, int(bool(on))))
+
+    def probe_compare_rate(self, iterations: int = 20000):
+        """Measured FP32 compares per second of the whole GPU (diagnostic)."""
+        rate = ctypes.c_double(0)
+        sms = ctypes.c_uint32(0)
+        self._check(self._L.sky_probe_compare_rate(self._h, int(iterations), ctypes.byref(rate), ctypes.byref(sms)))
+        return rate.value, sms.value
 
     def stats(self) -> dict:
         s = SkyStats()

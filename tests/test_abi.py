@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "skyline.h")).read()
+    src = "".join(open(os.path.join(ROOT, "include", h)).read() for h in ("skyline.h", "skyline_diag.h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(sky_[a-z_]+)\s*\(", src)))
 
