@@ -324,8 +324,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    # derived FP32 compare peak: 152 SMs x 128 lanes x 2.07 GHz
-    ap.add_argument("--compare-peak-tcmp", type=float, default=SM_COUNT * 128 * 2.07e9 / 1e12)
+    # FP32 compare peak: 152 SMs x 64 compare lanes per SM per clock x 2.07 GHz
+    # (the compare-rate probe of the library measures 58.6 per SM per clock)
+    ap.add_argument("--compare-peak-tcmp", type=float, default=SM_COUNT * 64 * 2.07e9 / 1e12)
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":

@@ -1,8 +1,9 @@
 // C ABI of libskyline (include/skyline.h): contexts, scratch memory and the
 // host-side orchestration of Algorithm 2 (Section 3) with the optimisations
 // of Sections 3.2 (Grid Filtering), 4.1 (Sorted representatives) and 4.2
-// (NoSeq).  Every step runs in the kernels of sky_prep.cu, sky_prims.cu and
-// sky_dom.cu; the host only sizes buffers, launches and copies results.
+// (NoSeq).  Every step runs in the kernels of sky_prep.cu, sky_prims.cu,
+// sky_dom.cu and sky_engine.cu; the host only sizes buffers, launches and
+// copies results.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -78,6 +79,7 @@ struct Bufs {
   u32* vals[2];
   u32* head;
   float* pts;
+  uint4* hc;
   float* score;
   u32* orig;
   u32* spid;
@@ -87,11 +89,16 @@ struct Bufs {
   u32* scan_tmp;
   u32* hist;
   float* win;
+  uint4* whc;
+  u32* dpos;
+  uint4* dhc;
   float* upts;
+  uint4* uhc;
   float* uscore;
   u32* upos;
   u32* useg;
   float* mpts;
+  uint4* mhc;
   float* mscore;
   u32* mpos;
   u8* malive;
@@ -99,8 +106,9 @@ struct Bufs {
   SegDesc* segs;
   SegState* st;
   u32* done_round;
-  u32* gdone;
-  u64 gcap;
+  u32* tdoneA;
+  u32* tdoneB;
+  u64 tcap;
   u32* ctl;
   u32* words;  // err, colmax[8], counters
   u8* clos;
@@ -134,6 +142,7 @@ size_t layout(const Plan& pl, u32 ang_words, char* base, Bufs* b) {
   b->vals[1] = c.take<u32>(n);
   b->head = c.take<u32>(n);
   b->pts = c.take<float>(n * 4 * V);
+  b->hc = c.take<uint4>(n);
   b->score = c.take<float>(n);
   b->orig = c.take<u32>(n);
   b->spid = c.take<u32>(n);
@@ -144,11 +153,16 @@ size_t layout(const Plan& pl, u32 ang_words, char* base, Bufs* b) {
   b->scan_tmp = c.take<u32>(scan_words);
   b->hist = c.take<u32>(radix_hist_words(n));
   b->win = c.take<float>(n * 4 * V);
+  b->whc = c.take<uint4>(n);
+  b->dpos = c.take<u32>(n);
+  b->dhc = c.take<uint4>(n);
   b->upts = c.take<float>(n * 4 * V);
+  b->uhc = c.take<uint4>(n);
   b->uscore = c.take<float>(n);
   b->upos = c.take<u32>(n);
   b->useg = c.take<u32>(P + 1);
   b->mpts = c.take<float>(n * 4 * V);
+  b->mhc = c.take<uint4>(n);
   b->mscore = c.take<float>(n);
   b->mpos = c.take<u32>(n);
   b->malive = c.take<u8>(n);
@@ -156,8 +170,9 @@ size_t layout(const Plan& pl, u32 ang_words, char* base, Bufs* b) {
   b->segs = c.take<SegDesc>(P);
   b->st = c.take<SegState>(2 * P);
   b->done_round = c.take<u32>(P);
-  b->gcap = engine_group_capacity(n, (u32)P);
-  b->gdone = c.take<u32>(b->gcap);
+  b->tcap = engine_tile_capacity(n, (u32)P);
+  b->tdoneA = c.take<u32>(b->tcap);
+  b->tdoneB = c.take<u32>(b->tcap);
   b->ctl = c.take<u32>(ENGINE_CTL_WORDS);
   b->words = c.take<u32>(W_WORDS);
   b->clos = c.take<u8>(P);
@@ -401,6 +416,7 @@ sky_status run(sky_ctx* ctx, const float* points, u64 n, u32 d, const sky_params
   ga.vals = b.vals[sel];
   ga.P = P;
   ga.pts = b.pts;
+  ga.hc = b.hc;
   ga.score = b.score;
   ga.orig = b.orig;
   ga.spid = b.spid;
@@ -434,23 +450,27 @@ sky_status run(sky_ctx* ctx, const float* points, u64 n, u32 d, const sky_params
   record(ctx, 3);
 
   // ---- ComputeLocalSet: u_i = Sky(r_i) for every partition
-  CK(launch_build_segs(b.seg_off, P, dropped, b.pts, b.score, b.alive, b.win, nullptr, D, b.segs, st));
-  CK(cudaMemsetAsync(b.gdone, 0, b.gcap * sizeof(u32), st));
+  SegArrays sa{b.pts, b.hc, b.score, b.alive, b.win, b.whc, b.dpos, b.dhc};
+  CK(launch_build_segs(b.seg_off, P, dropped, sa, D, b.segs, st));
+  CK(cudaMemsetAsync(b.tdoneA, 0, b.tcap * sizeof(u32), st));
+  CK(cudaMemsetAsync(b.tdoneB, 0, b.tcap * sizeof(u32), st));
   EngineWork ew;
   ew.st = b.st;
   ew.done_round = b.done_round;
-  ew.gdone = b.gdone;
-  ew.gcap = b.gcap;
+  ew.tdoneA = b.tdoneA;
+  ew.tdoneB = b.tdoneB;
+  ew.tcap = b.tcap;
   ew.ctl = b.ctl;
+  const u32* maxround = b.ctl + engine_max_round_word();
   record(ctx, 8);
   if (pl.exec == SKY_EXEC_PERSISTENT) {
-    CK(engine_run(b.segs, P, pl.V, pl.cfg, ew, err, st));
+    CK(engine_run(b.segs, P, pl.cfg, ew, err, st));
     record(ctx, 9);
-    CK(launch_fold_max(b.ctl, b.words + W_MAXROUND_LOCAL, st));
+    CK(launch_fold_max(maxround, b.words + W_MAXROUND_LOCAL, st));
   } else {
     for (u32 q = 0; q < P; ++q) {
-      CK(engine_run(b.segs + q, 1, pl.V, pl.cfg, ew, err, st));
-      CK(launch_fold_max(b.ctl, b.words + W_MAXROUND_LOCAL, st));
+      CK(engine_run(b.segs + q, 1, pl.cfg, ew, err, st));
+      CK(launch_fold_max(maxround, b.words + W_MAXROUND_LOCAL, st));
     }
     record(ctx, 9);
   }
@@ -463,7 +483,8 @@ sky_status run(sky_ctx* ctx, const float* points, u64 n, u32 d, const sky_params
     CK(cudaMemcpyAsync(b.words + W_NU, b.scan_tmp + scan_total_index(n), sizeof(u32), cudaMemcpyDeviceToDevice,
                        st));
     const bool seq = pl.merge == SKY_MERGE_SEQUENTIAL;
-    CK(launch_compact_u(b.alive, b.excl, n, D, b.pts, b.score, b.spid, b.upts, b.uscore, b.upos, nullptr,
+    CK(launch_compact_u(b.alive, b.excl, n, D, b.pts, b.hc, b.score, b.spid, b.upts, b.uhc, b.uscore, b.upos,
+                        nullptr,
                         seq ? b.keys[0] : nullptr, seq ? b.vals[0] : nullptr, st));
     if (seq) {
       CK(cudaMemcpyAsync(ctx->pinned, b.words + W_NU, sizeof(u32), cudaMemcpyDeviceToHost, st));
@@ -471,14 +492,17 @@ sky_status run(sky_ctx* ctx, const float* points, u64 n, u32 d, const sky_params
       const u64 nu = ctx->pinned[0];
       int msel = 0;
       CK(radix_sort(b.keys, b.vals, nu, 0, 32, b.hist, b.scan_tmp, st, &msel));
-      CK(launch_gather_u(b.vals[msel], nu, D, b.upts, b.uscore, b.upos, b.mpts, b.mscore, b.mpos, st));
+      CK(launch_gather_u(b.vals[msel], nu, D, b.upts, b.uhc, b.uscore, b.upos, b.mpts, b.mhc, b.mscore, b.mpos,
+                         st));
       CK(cudaMemsetAsync(b.malive, 1, nu ? nu : 1, st));
-      CK(launch_build_one_seg(b.mpts, b.mscore, b.malive, b.win, b.words + W_NU, D, b.segs, st));
-      CK(cudaMemsetAsync(b.gdone, 0, b.gcap * sizeof(u32), st));
+      SegArrays ma{b.mpts, b.mhc, b.mscore, b.malive, b.win, b.whc, b.dpos, b.dhc};
+      CK(launch_build_one_seg(ma, b.words + W_NU, D, b.segs, st));
+      CK(cudaMemsetAsync(b.tdoneA, 0, b.tcap * sizeof(u32), st));
+      CK(cudaMemsetAsync(b.tdoneB, 0, b.tcap * sizeof(u32), st));
       record(ctx, 10);
-      CK(engine_run(b.segs, 1, pl.V, pl.cfg, ew, err, st));
+      CK(engine_run(b.segs, 1, pl.cfg, ew, err, st));
       record(ctx, 11);
-      CK(launch_fold_max(b.ctl, b.words + W_MAXROUND_MERGE, st));
+      CK(launch_fold_max(maxround, b.words + W_MAXROUND_MERGE, st));
       CK(launch_scatter_alive(b.malive, b.mpos, nu, b.alive, b.stage_s, ST_MERGE, st));
     } else {
       CK(launch_useg(b.seg_off, P, b.excl, n, b.words + W_NU, b.useg, st));

@@ -1,32 +1,14 @@
-// Dominance kernels: the local-skyline engine (Algorithm 1, SFS, run on every
-// partition of Algorithm 2 at once), the representative filter (Section 4.1)
-// and the NoSeq final phase (Section 4.2).
+// Dominance kernels outside the local-skyline engine: the representative
+// filter (Section 4.1, a relative skyline: kill candidates dominated by a
+// point of a second set) and the NoSeq final phase (Section 4.2, Prop. 2),
+// plus the segment descriptors the engine (sky_engine.cu) runs on.
 //
-// Exactness rests on one fact: t is outside Sky(r) iff some point of r
-// dominates t, whether or not that point is itself in the skyline (a minimal
-// dominator exists because dominance is a strict partial order on a finite
-// set, and it is in the skyline).  So a candidate may be tested against any
-// superset of its skyline dominators -- dead points included -- and the
-// result is still exact.  Score order (f = attribute sum, monotone) bounds
-// where the dominators can be: s < t implies f(s) <= f(t).
-//
-// SFS in rounds.  The points of a segment are sorted by f.  A round takes
-// the next chunk of the segment (cut only between different scores) and
-// tests every chunk point against (a) the window -- the skyline points of
-// all earlier chunks, whose scores are strictly lower -- and (b) the chunk
-// points with score <= its own.  A minimal dominator of a chunk point is in
-// one of those two sets, so the chunk's survivors are exactly its skyline
-// points, and they are appended to the window.
-//
-// Work decomposition.  A group is 32 * R consecutive chunk points held in
-// the registers of one warp (R per lane).  A work item is (group, dominator
-// block of DB points); items are numbered dominator-block-major so that
-// early blocks (strongest window points) run first and later items find
-// their candidates already dead.  Each item's warp scans its block with
-// uniform loads, tests all R x 32 candidates per dominator with FP32
-// compares, and exits as soon as a warp ballot shows every candidate dead.
-// The last item to finish a group appends the group's survivors to the
-// window; the last group of a segment sets up the segment's next round.
+// Both kernels are exact for the same reason as the engine: t is outside
+// Sky(r) iff some point of r dominates t, so testing a candidate against any
+// set of real input points never kills a skyline point.  A group is 32 * R
+// candidates in the registers of one warp (R per lane); the warp scans its
+// dominators with uniform loads, tests every candidate with FP32 compares
+// (Def. 1) and leaves as soon as a ballot shows every candidate dead.
 #include <algorithm>
 #include <cstdio>
 #include "sky_internal.cuh"
@@ -40,58 +22,12 @@ constexpr int THREADS = WARPS * 32;
 constexpr int R = 2;             // candidates per lane
 constexpr int GS = 32 * R;       // candidates per group
 constexpr int IB = 4;            // items taken per atomic fetch
-constexpr u32 MAX_SEG = 8192;    // segments per engine launch
-constexpr u64 BARRIER_TIMEOUT_NS = 4000000000ull;
 
-// control words
-enum { C_ITEMS0 = 0, C_ITEMS1 = 1, C_BAR_COUNT = 2, C_BAR_GEN = 3, C_ABORT = 4, C_MAXROUND = 5,
-       C_NOSEQ_ITEMS = 6, C_REL_ITEMS = 7 };
+// control word of the NoSeq work counter (the engine uses words 0..7)
+constexpr int C_NOSEQ_ITEMS = 12;
 
-__device__ __forceinline__ u64 globaltimer() {
-  u64 t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ u32 ld_cg_u32(const u32* p) { return __ldcg(p); }
-__device__ __forceinline__ u32 ld_vol_u32(const u32* p) { return *(const volatile u32*)p; }
 __device__ __forceinline__ u8 ld_cg_u8(const u8* p) {
   return (u8)__ldcg(reinterpret_cast<const unsigned char*>(p));
-}
-
-// Grid-wide barrier of a cooperative launch (all blocks co-resident).  The
-// wait is bounded: after BARRIER_TIMEOUT_NS it sets ERR_TIMEOUT and the abort
-// word, and every block leaves the kernel at its next check.
-__device__ bool grid_barrier(u32* ctl, u32* err) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    u32 gen = ld_vol_u32(ctl + C_BAR_GEN);
-    __threadfence();
-    u32 arrived = atomicAdd(ctl + C_BAR_COUNT, 1u);
-    bool ok = true;
-    if (arrived == gridDim.x - 1) {
-      atomicExch(ctl + C_BAR_COUNT, 0u);
-      __threadfence();
-      atomicAdd(ctl + C_BAR_GEN, 1u);
-    } else {
-      u64 t0 = globaltimer();
-      while (ld_vol_u32(ctl + C_BAR_GEN) == gen) {
-        if (ld_vol_u32(ctl + C_ABORT)) { ok = false; break; }
-        if (globaltimer() - t0 > BARRIER_TIMEOUT_NS) {
-          atomicOr(err, ERR_TIMEOUT);
-          atomicExch(ctl + C_ABORT, 1u);
-          ok = false;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    s_ok = ok && !ld_vol_u32(ctl + C_ABORT);
-  }
-  __syncthreads();
-  return s_ok;
 }
 
 // ------------------------------------------------------------ dominance scan
@@ -204,264 +140,6 @@ __device__ __forceinline__ void store_kills(u8* alive, u32 base, int lane, const
 #pragma unroll
   for (int r = 0; r < R; ++r)
     if (was[r] && !c.alive[r]) alive[base + r * 32 + lane] = 0;
-}
-
-// First position >= from in [from, n) whose score exceeds v (scores sorted).
-__device__ __forceinline__ u32 upper_bound_score(const float* __restrict__ score, u32 from, u32 n, float v) {
-  u32 lo = from, hi = n;
-  while (lo < hi) {
-    u32 mid = lo + ((hi - lo) >> 1);
-    if (__ldg(score + mid) <= v) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
-
-// End of the chunk that starts at `start` with nominal length k: extended so
-// that a run of equal scores is never split.
-__device__ __forceinline__ u32 chunk_end(const SegDesc& sd, u32 start, u32 k) {
-  u64 e = (u64)start + k;
-  if (e >= sd.n) return sd.n;
-  return upper_bound_score(sd.score, (u32)e, sd.n, __ldg(sd.score + e - 1));
-}
-
-__device__ __forceinline__ u32 ceil_div(u32 a, u32 b) { return (a + b - 1) / b; }
-
-__device__ __forceinline__ void plan_round(const SegDesc& sd, const EngineCfg& cfg, SegState& s) {
-  if (s.cur >= sd.n) {
-    s.cend = sd.n;
-    s.groups = 0;
-    s.items = 0;
-    return;
-  }
-  u64 k = ((u64)s.wlen * cfg.alpha_x4) / 4;
-  k = k < cfg.chunk_min ? cfg.chunk_min : k;
-  k = k > cfg.chunk_max ? cfg.chunk_max : k;
-  s.cend = chunk_end(sd, s.cur, (u32)k);
-  u32 len = s.cend - s.cur;
-  s.groups = ceil_div(len, GS);
-  s.items = s.groups * (ceil_div(s.wlen, cfg.dom_block) + ceil_div(len, cfg.dom_block));
-}
-
-// Block-wide exclusive scan of vals (n entries) into out[0..n]; out[n] = total.
-__device__ void block_scan_to_smem(const SegState* st, const u32* done_round, u32 round, u32 n, bool groups,
-                                   u32* out) {
-  __shared__ u32 warp_tot[WARPS];
-  __shared__ u32 carry;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (u32 base = 0; base < n; base += THREADS) {
-    u32 i = base + threadIdx.x;
-    u32 v = 0;
-    // a segment that finished in an earlier round contributes nothing; one
-    // that finishes during this round keeps its count until the round ends
-    if (i < n && ld_cg_u32(done_round + i) > round)
-      v = groups ? ld_cg_u32(&st[i].groups) : ld_cg_u32(&st[i].items);
-    u32 x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      u32 y = __shfl_up_sync(FULL, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_tot[warp] = x;
-    __syncthreads();
-    u32 pre = carry;
-    for (int w2 = 0; w2 < warp; ++w2) pre += warp_tot[w2];
-    if (i < n) out[i] = pre + x - v;
-    __syncthreads();
-    if (threadIdx.x == THREADS - 1) carry = pre + x;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[n] = carry;
-  __syncthreads();
-}
-
-// ------------------------------------------------------------ engine
-
-struct EngineParams {
-  const SegDesc* segs;
-  u32 nseg;
-  EngineCfg cfg;
-  SegState* st;       // 2 * nseg, alternating by round parity
-  u32* done_round;    // nseg: first round in which the segment has no work
-  u32* gdone;
-  u64 gcap;
-  u32* ctl;
-  u32* err;
-};
-
-// One work item of the engine for segment sd: group g against dominator
-// block b of this round.
-template <int D>
-__device__ void engine_item(const EngineParams& P, const SegDesc& sd, u32 s, const SegState& S, u32 b,
-                            u32 g, u32 gid, SegState* cur, SegState* nxt, u32 round, int lane) {
-  constexpr int V = vec_of(D);
-  const u32 DB = P.cfg.dom_block;
-  const u32 wblocks = ceil_div(S.wlen, DB);
-  const u32 len = S.cend - S.cur;
-  const u32 cblocks = ceil_div(len, DB);
-  const u32 base = S.cur + g * GS;
-  const u32 gend = min(base + GS, S.cend);
-
-  Cand<D> c;
-  bool was[R];
-  load_cands<D>(sd.pts, sd.alive, base, gend, lane, c, was);
-  bool any = false;
-#pragma unroll
-  for (int r = 0; r < R; ++r) any |= c.alive[r];
-  if (__any_sync(FULL, any)) {
-    if (b < wblocks) {
-      u32 lo = b * DB;
-      u32 cnt = min(DB, S.wlen - lo);
-      scan_block<D>(sd.win + (u64)lo * V, cnt, true, c);
-    } else {
-      u32 lo = S.cur + (b - wblocks) * DB;
-      // chunk dominators with score <= the group's largest score
-      u32 hi = upper_bound_score(sd.score, gend - 1, S.cend, __ldg(sd.score + gend - 1));
-      hi = min(hi, lo + DB);
-      if (lo < hi) scan_block<D>(sd.pts + (u64)lo * V, hi - lo, false, c);
-    }
-    store_kills<D>(sd.alive, base, lane, c, was);
-  }
-
-  // completion of the group
-  __syncwarp();
-  u32 last = 0;
-  if (lane == 0) {
-    __threadfence();
-    u32 old = atomicAdd(P.gdone + gid, 1u);
-    last = (old == wblocks + cblocks - 1);
-    if (last) P.gdone[gid] = 0;
-  }
-  last = __shfl_sync(FULL, last, 0);
-  if (!last) return;
-  __threadfence();
-  // every item of the group is done: the flags are final
-  bool surv[R];
-  u32 cnt = 0;
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    u32 pos = base + r * 32 + lane;
-    surv[r] = pos < gend && ld_cg_u8(sd.alive + pos);
-    cnt += __popc(__ballot_sync(FULL, surv[r]));
-  }
-  u32 wbase = 0;
-  if (lane == 0 && cnt) wbase = atomicAdd(&cur[s].wfill, cnt);
-  wbase = __shfl_sync(FULL, wbase, 0);
-  u32 off = 0;
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    u32 m = __ballot_sync(FULL, surv[r]);
-    if (surv[r]) {
-      u32 slot = wbase + off + __popc(m & ((1u << lane) - 1u));
-      u32 pos = base + r * 32 + lane;
-      const float4* src = sd.pts + (u64)pos * V;
-      float4* dst = sd.win + (u64)slot * V;
-#pragma unroll
-      for (int v = 0; v < V; ++v) dst[v] = __ldg(src + v);
-      if (sd.wpos) sd.wpos[slot] = pos;
-    }
-    off += __popc(m);
-  }
-  __threadfence();
-  if (lane == 0) {
-    u32 old = atomicAdd(&cur[s].done_groups, 1u);
-    if (old == S.groups - 1) {
-      // last group of the segment: plan the next round
-      __threadfence();
-      SegState nx;
-      nx.cur = S.cend;
-      nx.wlen = atomicAdd(&cur[s].wfill, 0u);
-      nx.wfill = nx.wlen;
-      nx.done_groups = 0;
-      nx.rounds = S.rounds + 1;
-      plan_round(sd, P.cfg, nx);
-      nxt[s] = nx;
-      if (nx.items == 0) P.done_round[s] = round + 1;
-      atomicMax(P.ctl + C_MAXROUND, nx.rounds);
-    }
-  }
-}
-
-__global__ void __launch_bounds__(THREADS) k_engine(EngineParams P) {
-  extern __shared__ u32 sh[];
-  u32* s_items = sh;                  // nseg + 1
-  u32* s_groups = sh + (P.nseg + 1);  // nseg + 1
-  const int lane = threadIdx.x & 31;
-  const u32 nseg = P.nseg;
-
-  // round 0 plans
-  if (threadIdx.x == 0) {
-    for (u32 s = blockIdx.x; s < nseg; s += gridDim.x) {
-      SegState z;
-      z.cur = 0; z.wlen = 0; z.wfill = 0; z.done_groups = 0; z.rounds = 0;
-      plan_round(P.segs[s], P.cfg, z);
-      P.st[s] = z;
-      SegState y = z;
-      y.items = 0;
-      y.groups = 0;
-      P.st[nseg + s] = y;
-      P.done_round[s] = z.items ? 0xffffffffu : 0u;
-    }
-  }
-  if (!grid_barrier(P.ctl, P.err)) return;
-
-  for (u32 round = 0;; ++round) {
-    SegState* cur = P.st + (round & 1) * nseg;
-    SegState* nxt = P.st + ((round + 1) & 1) * nseg;
-    block_scan_to_smem(cur, P.done_round, round, nseg, false, s_items);
-    block_scan_to_smem(cur, P.done_round, round, nseg, true, s_groups);
-    const u32 total = s_items[nseg];
-    if (total == 0) break;
-    if (s_groups[nseg] > P.gcap) {
-      if (threadIdx.x == 0) {
-        atomicOr(P.err, ERR_CAPACITY);
-        atomicExch(P.ctl + C_ABORT, 1u);
-      }
-      return;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) P.ctl[(round + 1) & 1] = 0;
-    u32* counter = P.ctl + (round & 1);
-    for (;;) {
-      u32 first = 0;
-      if (lane == 0) first = atomicAdd(counter, (u32)IB);
-      first = __shfl_sync(FULL, first, 0);
-      if (first >= total) break;
-      u32 lim = min(first + IB, total);
-      for (u32 it = first; it < lim; ++it) {
-        // segment of item `it`: last s with s_items[s] <= it
-        u32 lo = 0, hi = nseg;
-        while (hi - lo > 1) {
-          u32 mid = (lo + hi) >> 1;
-          if (s_items[mid] <= it) lo = mid;
-          else hi = mid;
-        }
-        const u32 s = lo;
-        const SegDesc sd = P.segs[s];
-        SegState S;
-        S.cur = ld_cg_u32(&cur[s].cur);
-        S.cend = ld_cg_u32(&cur[s].cend);
-        S.wlen = ld_cg_u32(&cur[s].wlen);
-        S.groups = ld_cg_u32(&cur[s].groups);
-        S.rounds = ld_cg_u32(&cur[s].rounds);
-        u32 l = it - s_items[s];
-        u32 b = l / S.groups, g = l % S.groups;
-        u32 gid = s_groups[s] + g;
-        switch (sd.d) {
-          case 1: engine_item<1>(P, sd, s, S, b, g, gid, cur, nxt, round, lane); break;
-          case 2: engine_item<2>(P, sd, s, S, b, g, gid, cur, nxt, round, lane); break;
-          case 3: engine_item<3>(P, sd, s, S, b, g, gid, cur, nxt, round, lane); break;
-          case 4: engine_item<4>(P, sd, s, S, b, g, gid, cur, nxt, round, lane); break;
-          case 5: engine_item<5>(P, sd, s, S, b, g, gid, cur, nxt, round, lane); break;
-          case 6: engine_item<6>(P, sd, s, S, b, g, gid, cur, nxt, round, lane); break;
-          case 7: engine_item<7>(P, sd, s, S, b, g, gid, cur, nxt, round, lane); break;
-          default: engine_item<8>(P, sd, s, S, b, g, gid, cur, nxt, round, lane); break;
-        }
-      }
-    }
-    if (!grid_barrier(P.ctl, P.err)) return;
-  }
 }
 
 // ------------------------------------------------------------ relative skyline
@@ -594,33 +272,38 @@ __global__ void k_noseq_groups(const u32* __restrict__ useg, u32 P, u32* __restr
 }
 
 // Segment descriptors of the local phase from the partition offsets;
-// partitions removed by Grid Filtering get no work.
-__global__ void k_build_segs(const u32* __restrict__ seg_off, u32 P, const u8* __restrict__ dropped,
-                             const float4* pts, const float* score, u8* alive, float4* win, u32* wpos,
+// partitions removed by Grid Filtering get no work.  Every per-point array
+// of a segment is the slice [seg_off[s], seg_off[s + 1]) of the whole array.
+__global__ void k_build_segs(const u32* __restrict__ seg_off, u32 P, const u8* __restrict__ dropped, SegArrays a,
                              int d, SegDesc* segs) {
   u64 s = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= P) return;
   const int V = vec_of(d);
   u32 o = seg_off[s];
   SegDesc sd;
-  sd.pts = pts + (u64)o * V;
-  sd.score = score + o;
-  sd.alive = alive + o;
-  sd.win = win + (u64)o * V;
-  sd.wpos = wpos ? wpos + o : nullptr;
+  sd.pts = reinterpret_cast<const float4*>(a.pts) + (u64)o * V;
+  sd.hc = a.hc + o;
+  sd.score = a.score + o;
+  sd.alive = a.alive + o;
+  sd.win = reinterpret_cast<float4*>(a.win) + (u64)o * V;
+  sd.whc = a.whc + o;
+  sd.dpos = a.dpos + o;
+  sd.dhc = a.dhc + o;
   sd.n = (dropped && dropped[s]) ? 0u : seg_off[s + 1] - o;
   sd.d = (u32)d;
   segs[s] = sd;
 }
 
-__global__ void k_build_one_seg(const float4* pts, const float* score, u8* alive, float4* win,
-                                const u32* n_dev, int d, SegDesc* seg) {
+__global__ void k_build_one_seg(SegArrays a, const u32* n_dev, int d, SegDesc* seg) {
   SegDesc sd;
-  sd.pts = pts;
-  sd.score = score;
-  sd.alive = alive;
-  sd.win = win;
-  sd.wpos = nullptr;
+  sd.pts = reinterpret_cast<const float4*>(a.pts);
+  sd.hc = a.hc;
+  sd.score = a.score;
+  sd.alive = a.alive;
+  sd.win = reinterpret_cast<float4*>(a.win);
+  sd.whc = a.whc;
+  sd.dpos = a.dpos;
+  sd.dhc = a.dhc;
   sd.n = *n_dev;
   sd.d = (u32)d;
   *seg = sd;
@@ -632,26 +315,23 @@ int g_sm_count = 0;
 
 }  // namespace
 
-cudaError_t launch_build_segs(const u32* seg_off, u32 P, const u8* dropped, const float* pts, const float* score,
-                              u8* alive, float* win, u32* wpos, int d, SegDesc* segs, cudaStream_t st) {
+cudaError_t launch_build_segs(const u32* seg_off, u32 P, const u8* dropped, const SegArrays& a, int d,
+                              SegDesc* segs, cudaStream_t st) {
   if (P == 0) return cudaSuccess;
   note_launch();
-  k_build_segs<<<(P + 255) / 256, 256, 0, st>>>(seg_off, P, dropped, reinterpret_cast<const float4*>(pts), score,
-                                                alive, reinterpret_cast<float4*>(win), wpos, d, segs);
+  k_build_segs<<<(P + 255) / 256, 256, 0, st>>>(seg_off, P, dropped, a, d, segs);
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_one_seg(const float* pts, const float* score, u8* alive, float* win, const u32* n_dev,
-                                 int d, SegDesc* seg, cudaStream_t st) {
+cudaError_t launch_build_one_seg(const SegArrays& a, const u32* n_dev, int d, SegDesc* seg, cudaStream_t st) {
   note_launch();
-  k_build_one_seg<<<1, 1, 0, st>>>(reinterpret_cast<const float4*>(pts), score, alive,
-                                   reinterpret_cast<float4*>(win), n_dev, d, seg);
+  k_build_one_seg<<<1, 1, 0, st>>>(a, n_dev, d, seg);
   return cudaGetLastError();
 }
 
-cudaError_t launch_fold_max(const u32* ctl, u32* dst, cudaStream_t st) {
+cudaError_t launch_fold_max(const u32* src, u32* dst, cudaStream_t st) {
   note_launch();
-  k_fold_max<<<1, 1, 0, st>>>(ctl + C_MAXROUND, dst);
+  k_fold_max<<<1, 1, 0, st>>>(src, dst);
   return cudaGetLastError();
 }
 
@@ -662,55 +342,6 @@ int device_sm_count() {
   cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
   g_sm_count = n;
   return n;
-}
-
-u64 engine_group_capacity(u64 total_points, u32 nseg) { return total_points / GS + nseg + 1; }
-
-cudaError_t engine_run(const SegDesc* segs_dev, u32 nseg, u32 max_vec, const EngineCfg& cfg,
-                       const EngineWork& w, u32* err, cudaStream_t st) {
-  (void)max_vec;
-  if (nseg == 0) return cudaSuccess;
-  if (nseg > MAX_SEG) {
-    // more segments than one launch's shared-memory prefix holds: batches
-    for (u32 s0 = 0; s0 < nseg; s0 += MAX_SEG) {
-      cudaError_t e = engine_run(segs_dev + s0, std::min(MAX_SEG, nseg - s0), max_vec, cfg, w, err, st);
-      if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-  }
-  EngineParams P;
-  P.segs = segs_dev;
-  P.nseg = nseg;
-  P.cfg = cfg;
-  P.st = w.st;
-  P.done_round = w.done_round;
-  P.gdone = w.gdone;
-  P.gcap = w.gcap;
-  P.ctl = w.ctl;
-  P.err = err;
-  size_t smem = 2 * (size_t)(nseg + 1) * sizeof(u32);
-  cudaError_t e = cudaFuncSetAttribute(k_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_engine, THREADS, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm <= 0) return cudaErrorInvalidConfiguration;
-  int sms = g_sm_count ? g_sm_count : device_sm_count();
-  unsigned grid = (unsigned)(sms * per_sm);
-  e = cudaMemsetAsync(w.ctl, 0, ENGINE_CTL_WORDS * sizeof(u32), st);
-  if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t lc = {};
-  lc.gridDim = dim3(grid);
-  lc.blockDim = dim3(THREADS);
-  lc.dynamicSmemBytes = smem;
-  lc.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  lc.attrs = attr;
-  lc.numAttrs = 1;
-  note_launch();
-  return cudaLaunchKernelEx(&lc, k_engine, P);
 }
 
 cudaError_t launch_relative(const float* cand, u8* alive, u64 nc, const float* dom, u32 nd_host,

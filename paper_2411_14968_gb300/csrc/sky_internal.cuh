@@ -117,6 +117,7 @@ struct GatherArgs {
   const u32* vals;       // sorted point indices
   u32 P;                 // partitions
   float* pts;            // out: padded points in sorted order, vec_of(d) float4 each
+  uint4* hc;             // out: FP16 images of the points
   float* score;          // out: scores in sorted order
   u32* orig;             // out: original index of sorted position
   u32* spid;             // out: partition of sorted position
@@ -143,14 +144,15 @@ cudaError_t launch_rep_select(const u32* seg_off, u32 P, u32 k, const u8* droppe
 
 // Compaction of the points alive after the local phase into u (keeps the
 // (partition, score, index) order).
-cudaError_t launch_compact_u(const u8* alive, const u32* excl, u64 n, int d, const float* pts,
-                             const float* score, const u32* spid, float* upts, float* uscore,
+cudaError_t launch_compact_u(const u8* alive, const u32* excl, u64 n, int d, const float* pts, const uint4* hc,
+                             const float* score, const u32* spid, float* upts, uint4* uhc, float* uscore,
                              u32* upos, u32* upid, u64* ukey, u32* uval, cudaStream_t st);
 // useg[s] = offset of u_s in u (P + 1 entries); total = device pointer to |u|.
 cudaError_t launch_useg(const u32* seg_off, u32 P, const u32* excl, u64 n, const u32* total, u32* useg,
                         cudaStream_t st);
-cudaError_t launch_gather_u(const u32* order, u64 n, int d, const float* upts, const float* uscore,
-                            const u32* upos, float* mpts, float* mscore, u32* mpos, cudaStream_t st);
+cudaError_t launch_gather_u(const u32* order, u64 n, int d, const float* upts, const uint4* uhc,
+                            const float* uscore, const u32* upos, float* mpts, uint4* mhc, float* mscore,
+                            u32* mpos, cudaStream_t st);
 // Points dead in a merge array: their sorted-position flag is cleared and,
 // if no stage was recorded yet, stage `code` is recorded.
 cudaError_t launch_scatter_alive(const u8* malive, const u32* mpos, u64 n, u8* alive, u8* stage_s,
@@ -166,29 +168,38 @@ cudaError_t launch_compact_reps(const u8* rep_alive, const u32* excl, u32 nrep, 
                                 float* kept_pts, cudaStream_t st);
 cudaError_t launch_stage_hist(const u8* stage_s, u64 n, u32* hist6, cudaStream_t st);
 
-// ---------------------------------------------------------------- dominance engine (sky_dom.cu)
+// ---------------------------------------------------------------- dominance engine (sky_engine.cu)
+// FP16 images of a point's attributes: __float2half_rd of each attribute,
+// packed two per 32-bit word (attribute 2k in the low half), +0 padding.
+// Round-down is monotone, so w[a] > t[a] whenever code(w)[a] > code(t)[a].
+//
 // One segment (a partition, or the whole merge input) of the SFS engine.
-// The points of a segment are sorted by score; `win` has room for n points.
+// The points of a segment are sorted by score; win/whc and dpos/dhc have
+// room for n entries each.
 struct SegDesc {
   const float4* pts;     // vec_of(d) float4 per point, sorted by score
+  const uint4* hc;       // FP16 images of pts
   const float* score;
   u8* alive;
-  float4* win;           // window: skyline points found so far (vec float4 per point)
-  u32* wpos;             // segment-relative position of each window point (may be null)
+  float4* win;           // window: skyline points found so far (FP32)
+  uint4* whc;            // window FP16 images
+  u32* dpos;             // dense list of the round: segment-relative positions
+  uint4* dhc;            // dense list FP16 images
   u32 n;
   u32 d;                 // attributes (1..8)
 };
 
 // Round state of a segment (two copies, alternating by round parity).
 struct SegState {
-  u32 cur;          // first position of the current chunk
-  u32 cend;         // end of the current chunk (never splits a run of equal scores)
-  u32 wlen;         // window points visible to this round
-  u32 wfill;        // window append cursor (atomic)
-  u32 groups;       // candidate groups of the chunk
-  u32 items;        // work items of this round (groups x dominator blocks)
-  u32 done_groups;  // groups finished (atomic)
-  u32 rounds;       // rounds completed
+  u32 cur;      // first position of the current chunk
+  u32 cend;     // end of the current chunk (never splits a run of equal scores)
+  u32 wlen;     // window points visible to this round
+  u32 wfill;    // window append cursor (atomic)
+  u32 tiles;    // candidate tiles of the chunk (phase A)
+  u32 dlen;     // dense-list length after phase A (atomic)
+  u32 done_a;   // phase-A tiles finished (atomic)
+  u32 done_b;   // phase-B tiles finished (atomic)
+  u32 rounds;   // rounds completed
 };
 
 struct EngineCfg {
@@ -198,23 +209,37 @@ struct EngineCfg {
 struct EngineWork {
   SegState* st;       // 2 * nseg
   u32* done_round;    // nseg
-  u32* gdone;         // engine_group_capacity(...) counters, zero before the first launch
-  u64 gcap;
+  u32* tdoneA;        // engine_tile_capacity(...) counters, zero before the first launch
+  u32* tdoneB;        // same
+  u64 tcap;
   u32* ctl;           // ENGINE_CTL_WORDS control words
 };
 constexpr int ENGINE_CTL_WORDS = 16;
-u64 engine_group_capacity(u64 total_points, u32 nseg);
+u64 engine_tile_capacity(u64 total_points, u32 nseg);
+// Control word that receives the largest round count of a launch.
+u32 engine_max_round_word();
 
 // Local skylines of segs[0..nseg) in one cooperative launch (grid = the
 // co-resident capacity).  Kills dominated points (alive = 0) and leaves each
-// segment's skyline in its window.  ctl[5] receives the largest round count.
-cudaError_t engine_run(const SegDesc* segs_dev, u32 nseg, u32 max_vec, const EngineCfg& cfg,
-                       const EngineWork& w, u32* err, cudaStream_t st);
-cudaError_t launch_build_segs(const u32* seg_off, u32 P, const u8* dropped, const float* pts, const float* score,
-                              u8* alive, float* win, u32* wpos, int d, SegDesc* segs, cudaStream_t st);
-cudaError_t launch_build_one_seg(const float* pts, const float* score, u8* alive, float* win, const u32* n_dev,
-                                 int d, SegDesc* seg, cudaStream_t st);
-cudaError_t launch_fold_max(const u32* ctl, u32* dst, cudaStream_t st);
+// segment's skyline in its window.
+cudaError_t engine_run(const SegDesc* segs_dev, u32 nseg, const EngineCfg& cfg, const EngineWork& w, u32* err,
+                       cudaStream_t st);
+
+// Segment descriptors (sky_dom.cu).
+struct SegArrays {
+  const float* pts;
+  const uint4* hc;
+  const float* score;
+  u8* alive;
+  float* win;
+  uint4* whc;
+  u32* dpos;
+  uint4* dhc;
+};
+cudaError_t launch_build_segs(const u32* seg_off, u32 P, const u8* dropped, const SegArrays& a, int d,
+                              SegDesc* segs, cudaStream_t st);
+cudaError_t launch_build_one_seg(const SegArrays& a, const u32* n_dev, int d, SegDesc* seg, cudaStream_t st);
+cudaError_t launch_fold_max(const u32* src, u32* dst, cudaStream_t st);
 
 // Relative skyline (Section 4.2 definition): kill every alive candidate of
 // cand[0..nc) dominated by one of dom[0..nd) (nd = *nd_dev if given, else

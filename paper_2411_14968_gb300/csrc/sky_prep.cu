@@ -3,6 +3,7 @@
 // Filtering (Section 3.2), Sorted representatives (Section 4.1), compaction
 // of the local skylines and the final compaction into ascending indices.
 #include <algorithm>
+#include <cuda_fp16.h>
 #include "sky_internal.cuh"
 
 namespace sky {
@@ -21,6 +22,15 @@ __device__ __forceinline__ float score_of(const float (&x)[8]) {
 #pragma unroll
   for (int a = 1; a < D; ++a) f = __fadd_rn(f, x[a]);
   return f;
+}
+
+// FP16 round-down images of the 8 (padded) attributes, two per word.
+__device__ __forceinline__ u32 pack_rd(float lo, float hi) {
+  __half a = __float2half_rd(lo), b = __float2half_rd(hi);
+  return (u32)__half_as_ushort(a) | ((u32)__half_as_ushort(b) << 16);
+}
+__device__ __forceinline__ uint4 fp16_codes(const float (&x)[8]) {
+  return make_uint4(pack_rd(x[0], x[1]), pack_rd(x[2], x[3]), pack_rd(x[4], x[5]), pack_rd(x[6], x[7]));
 }
 
 // Reads point i of the row-major input with -0.0 turned into +0.0 (x + 0.0
@@ -213,6 +223,7 @@ __global__ void k_gather(GatherArgs g) {
   float4* dst = reinterpret_cast<float4*>(g.pts) + r * V;
   dst[0] = make_float4(x[0], x[1], x[2], x[3]);
   if (V > 1) dst[1] = make_float4(x[4], x[5], x[6], x[7]);
+  g.hc[r] = fp16_codes(x);
   g.score[r] = score_of<D>(x);
   g.orig[r] = i;
   g.alive[r] = 1;
@@ -334,9 +345,10 @@ __global__ void k_stage_hist(const u8* __restrict__ stage_s, u64 n, u32* hist6) 
 // index) order.
 template <int D>
 __global__ void k_compact_u(const u8* __restrict__ alive, const u32* __restrict__ excl, u64 n,
-                            const float* __restrict__ pts, const float* __restrict__ score,
-                            const u32* __restrict__ spid, float* __restrict__ upts,
-                            float* __restrict__ uscore, u32* __restrict__ upos, u32* __restrict__ upid,
+                            const float* __restrict__ pts, const uint4* __restrict__ hc,
+                            const float* __restrict__ score, const u32* __restrict__ spid,
+                            float* __restrict__ upts, uint4* __restrict__ uhc, float* __restrict__ uscore,
+                            u32* __restrict__ upos, u32* __restrict__ upid,
                             u64* __restrict__ ukey, u32* __restrict__ uval) {
   u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n || !alive[r]) return;
@@ -346,6 +358,7 @@ __global__ void k_compact_u(const u8* __restrict__ alive, const u32* __restrict_
   float4* dst = reinterpret_cast<float4*>(upts) + (u64)j * V;
 #pragma unroll
   for (int v = 0; v < V; ++v) dst[v] = src[v];
+  uhc[j] = hc[r];
   float f = score[r];
   uscore[j] = f;
   upos[j] = (u32)r;
@@ -367,8 +380,9 @@ __global__ void k_useg(const u32* __restrict__ seg_off, u32 P, const u32* __rest
 // u in score order for the sequential final phase.
 template <int D>
 __global__ void k_gather_u(const u32* __restrict__ order, u64 n, const float* __restrict__ upts,
-                           const float* __restrict__ uscore, const u32* __restrict__ upos,
-                           float* __restrict__ mpts, float* __restrict__ mscore, u32* __restrict__ mpos) {
+                           const uint4* __restrict__ uhc, const float* __restrict__ uscore,
+                           const u32* __restrict__ upos, float* __restrict__ mpts, uint4* __restrict__ mhc,
+                           float* __restrict__ mscore, u32* __restrict__ mpos) {
   u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   u32 j = order[r];
@@ -377,6 +391,7 @@ __global__ void k_gather_u(const u32* __restrict__ order, u64 n, const float* __
   float4* dst = reinterpret_cast<float4*>(mpts) + r * V;
 #pragma unroll
   for (int v = 0; v < V; ++v) dst[v] = src[v];
+  mhc[r] = uhc[j];
   mscore[r] = uscore[j];
   mpos[r] = upos[j];
 }
@@ -509,14 +524,14 @@ cudaError_t launch_stage_hist(const u8* stage_s, u64 n, u32* hist6, cudaStream_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_compact_u(const u8* alive, const u32* excl, u64 n, int d, const float* pts,
-                             const float* score, const u32* spid, float* upts, float* uscore,
+cudaError_t launch_compact_u(const u8* alive, const u32* excl, u64 n, int d, const float* pts, const uint4* hc,
+                             const float* score, const u32* spid, float* upts, uint4* uhc, float* uscore,
                              u32* upos, u32* upid, u64* ukey, u32* uval, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   return dispatch_d(d, [&](auto D) {
     note_launch();
-    k_compact_u<decltype(D)::value><<<grid_for(n), PT, 0, st>>>(alive, excl, n, pts, score, spid, upts,
-                                                               uscore, upos, upid, ukey, uval);
+    k_compact_u<decltype(D)::value><<<grid_for(n), PT, 0, st>>>(alive, excl, n, pts, hc, score, spid, upts,
+                                                               uhc, uscore, upos, upid, ukey, uval);
   });
 }
 
@@ -527,13 +542,14 @@ cudaError_t launch_useg(const u32* seg_off, u32 P, const u32* excl, u64 n, const
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_u(const u32* order, u64 n, int d, const float* upts, const float* uscore,
-                            const u32* upos, float* mpts, float* mscore, u32* mpos, cudaStream_t st) {
+cudaError_t launch_gather_u(const u32* order, u64 n, int d, const float* upts, const uint4* uhc,
+                            const float* uscore, const u32* upos, float* mpts, uint4* mhc, float* mscore,
+                            u32* mpos, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   return dispatch_d(d, [&](auto D) {
     note_launch();
-    k_gather_u<decltype(D)::value><<<grid_for(n), PT, 0, st>>>(order, n, upts, uscore, upos, mpts, mscore,
-                                                              mpos);
+    k_gather_u<decltype(D)::value><<<grid_for(n), PT, 0, st>>>(order, n, upts, uhc, uscore, upos, mpts, mhc,
+                                                              mscore, mpos);
   });
 }
 

@@ -89,6 +89,34 @@ def test_multi_round_small_chunks(ctx, oracle_mod):
                    chunk_alpha_x4=3, dom_block=64)
 
 
+def test_engine_tiles_and_blocks(ctx, oracle_mod):
+    # chunks of several candidate tiles, dense lists of several tiles, one or
+    # many window blocks per round
+    x = datagen.anticorrelated(60000, 6, 11)
+    for scheme, p, sl in (("none", 1, None), ("sliced", 3, None)):
+        for db in (128, 2048):
+            _check(ctx, oracle_mod, x, scheme, p, sl, chunk_min=3000, chunk_max=9000, dom_block=db)
+
+
+def test_fp16_image_collisions(ctx, oracle_mod):
+    # The engine rejects pairs on FP16 round-down images before the FP32
+    # test.  (a) every attribute in [1, 1 + 2^-10): all points share one FP16
+    # image, so FP32 decides every test; (b) magnitudes beyond the FP16 range
+    # (round-down saturates at 65504 or goes to -inf) and negative values.
+    rng = np.random.default_rng(12)
+    n = 4000
+    a = (1.0 + rng.integers(0, 512, (n, 4)) * 2.0 ** -23).astype(np.float32)
+    b = (rng.standard_normal((n, 5)) * 1e6).astype(np.float32)
+    b[::7, 2] = np.float32(3e38)
+    b[::11, 1] = np.float32(-3e38)
+    b[::13, 4] = np.float32(70000.0)
+    b[::17, 4] = np.float32(65504.0)
+    for x in (a, b):
+        for scheme, p in (("none", 1), ("sliced", 4), ("random", 8)):
+            _check(ctx, oracle_mod, x, scheme, p, rep="sorted", dom_block=128)
+            _check(ctx, oracle_mod, x, scheme, p, merge="noseq")
+
+
 def test_quantised_ties(ctx, oracle_mod):
     # many equal scores and exact duplicates: chunk cuts must not split runs
     for kind in ("independent", "correlated"):
