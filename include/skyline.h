@@ -158,6 +158,35 @@ const char* sky_last_error(sky_ctx* ctx);
 /* Frees the context and its device memory (synchronises its stream first). */
 void sky_destroy(sky_ctx* ctx);
 
+/* Largest N accepted by sky_skyline_static. */
+#define SKY_STATIC_MAX_POINTS 65536u
+
+/* The paper has no counterpart to this call: it serves callers that cannot
+   allocate device memory when they need a skyline -- code running under an
+   allocator that owns all of the GPU's memory and forbids cudaMalloc, a
+   latency-critical loop in which an allocation or the synchronisation of a
+   cudaFree is not acceptable, or code that must keep a fixed footprint.
+   It needs no context and allocates nothing: its scratch (about 2.4 MB) is
+   one file-scope device array of the library, reserved on every GPU that
+   loads the library until the process exits.
+
+   Sky(points) (Def. 1) of a small point set: points is device memory of the
+   current device, row-major N x d FP32, read-only; out_idx is device memory
+   of capacity >= N and receives the |Sky| ascending indices; *out_count
+   (host) receives |Sky|.  The work runs on cuda_stream (NULL = legacy
+   default stream) and the call blocks until it is done.  Errors:
+   SKY_EINVAL for d outside 1..8, N > SKY_STATIC_MAX_POINTS, NULL or host
+   pointers, or a NaN attribute; SKY_ECUDA if a CUDA call fails.  N = 0
+   returns SKY_OK with count 0.  The result equals sky_skyline's.
+
+   The first call on a device looks up the array's device address on that
+   device (the current one) and caches it, so it should come before any
+   stream capture.  Every call reuses the same array, so calls whose work
+   overlaps on the GPU -- from several host threads or on several streams
+   at once -- race and must not be made. */
+sky_status sky_skyline_static(const float* points, uint64_t n, uint32_t d, uint32_t* out_idx,
+                              uint64_t* out_count, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

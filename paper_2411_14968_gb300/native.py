@@ -73,7 +73,7 @@ class SkyStats(ctypes.Structure):
 
 EXPORTS = ["sky_params_init", "sky_create", "sky_set_stream", "sky_set_timing", "sky_skyline",
            "sky_skyline_ex", "sky_get_stats", "sky_status_str", "sky_last_error", "sky_destroy",
-           "sky_probe_compare_rate"]
+           "sky_probe_compare_rate", "sky_skyline_static"]
 
 _lock = threading.Lock()
 _lib = None
@@ -122,6 +122,8 @@ def load(build_if_missing: bool = True):
         L.sky_destroy.restype = None
         L.sky_probe_compare_rate.argtypes = [P, u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32)]
         L.sky_probe_compare_rate.restype = i32
+        L.sky_skyline_static.argtypes = [P, u64, u32, P, ctypes.POINTER(u64), P]
+        L.sky_skyline_static.restype = i32
         _lib = L
         return L
 
@@ -255,6 +257,34 @@ class Context:
         if with_diag:
             return res[: cnt.value], pid[:n], stage[:n]
         return res[: cnt.value]
+
+
+STATIC_MAX_POINTS = 65536
+
+
+def skyline_static(points, out=None):
+    """Sky(points) through sky_skyline_static, the entry point that allocates
+    no device memory (for callers that cannot call cudaMalloc).  points: a
+    CUDA float32 [N, d] tensor with N <= STATIC_MAX_POINTS; runs on the
+    tensor's current stream.  Returns a CUDA int32 tensor of ascending
+    indices (a view of `out` if given, which must be device memory of
+    capacity >= N).  Raises SkylineError on a non-OK status."""
+    import torch
+    L = load()
+    if not _is_cuda_tensor(points) or points.dtype != torch.float32 or points.dim() != 2:
+        raise ValueError("points must be a CUDA float32 [N, d] tensor")
+    points = points.contiguous()
+    n, d = points.shape
+    if out is None:
+        out = torch.empty(max(n, 1), dtype=torch.int32, device=points.device)
+    cnt = ctypes.c_uint64(0)
+    stream = torch.cuda.current_stream(points.device).cuda_stream
+    with torch.cuda.device(points.device):
+        st = L.sky_skyline_static(ctypes.c_void_p(points.data_ptr()), n, d, ctypes.c_void_p(out.data_ptr()),
+                                  ctypes.byref(cnt), ctypes.c_void_p(stream))
+    if st != SKY_OK:
+        raise SkylineError(st, L.sky_status_str(st).decode())
+    return out[: cnt.value]
 
 
 _default_ctx = None
