@@ -3,13 +3,17 @@
 
 Workload: 1,000,000 anticorrelated FP32 points, d = 6 (seeded synthetic
 data; the paper's own generator is unstated).  One step runs four exact
-skyline queries over the device-resident input, the partitioned method
+skyline queries over the device-resident input -- the partitioned method
 with Sliced (p = 64) and Angular (m = 4,2,2,2,2 -> p = 64) partitioning,
-each without and with Sorted representatives (1 per partition), every local
-skyline of a query in one persistent cooperative launch and the sequential
-final merge.  The metric is input points per second at the exact result
-(4 x N points per step).  The same step with one launch per partition is
-reported as `plain`; `e2e` runs it through the C ABI from host buffers.
+each without and with Sorted representatives (1 per partition), sequential
+final merge -- as one batch: every local skyline of the four queries in one
+persistent engine launch, the four merges in a second.  The metric is input
+points per second at the exact result (4 x N points per step).  Reported
+beside it: the same four queries one at a time (`per_query_persistent`),
+one at a time with one launch per partition (`plain`), the batch through the
+C ABI from pinned host buffers (`e2e`), and a serving leg that replays a
+Poisson arrival trace of mixed queries through the continuous-batching loop
+and through the one-query-at-a-time plain path (p50/p99 latency).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 Under torchrun every rank runs the same workload on its own GPU (replicas;
@@ -156,6 +160,102 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+SERVE_QUERIES = 300
+SERVE_SEED = 5
+
+
+def serving_pool(dev_pin: bool):
+    """Seeded datasets the serving queries are drawn from: per (kind, d) one
+    pool of 2^20 i.i.d. points; a query of N points is a window of N
+    consecutive rows at a seeded offset (rows are i.i.d., so a window is a
+    sample of the same distribution)."""
+    import torch
+    from paper_2411_14968_gb300 import datagen
+    pool = {}
+    for kind in ("anticorrelated", "independent"):
+        for d in range(3, 9):
+            if kind == "anticorrelated":
+                x = datagen.anticorrelated(1 << 20, d, 900 + d)
+            else:
+                x = datagen.independent(1 << 20, d, 950 + d, quantised=False)
+            t = torch.from_numpy(x)
+            pool[(kind, d)] = t.pin_memory().numpy() if dev_pin else x
+    return pool
+
+
+def serving_queries(num: int, pool, native):
+    from paper_2411_14968_gb300 import datagen
+    rng = np.random.default_rng(SERVE_SEED)
+    out = []
+    for kind, n, d, _ in datagen.serving_trace(num, SERVE_SEED):
+        base = pool[(kind, d)]
+        off = int(rng.integers(0, base.shape[0] - n + 1))
+        p = max(1, min(64, n // 8192))
+        out.append((base[off: off + n], p))
+    return out
+
+
+def run_serving(ctx, native, queries, arrivals, exec_, workers, max_batch):
+    """Replays the arrivals (seconds from start; None = all at once) through
+    the serving loop; returns per-query latency (ms) and the makespan (s)."""
+    ctx.serve_start(workers=workers, max_batch=max_batch)
+    params = [native.make_params(scheme="sliced" if p > 1 else "none", p=p, exec=exec_) for _, p in queries]
+    tickets = [None] * len(queries)
+    t0 = time.perf_counter()
+    for i, (x, _) in enumerate(queries):
+        if arrivals is not None:
+            dt = arrivals[i] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+        tickets[i] = ctx.submit(x, params[i])
+    lat, batch = [], []
+    for t in tickets:
+        _, info = ctx.wait(t)
+        lat.append(info["latency_us"] / 1e3)
+        batch.append(info["batch_queries"])
+    span = time.perf_counter() - t0
+    ctx.serve_stop()
+    return np.array(lat), span, float(np.mean(batch))
+
+
+def serving_leg(native, local):
+    """Continuous batching vs one query at a time with one launch per
+    partition, on the same Poisson arrival trace."""
+    from paper_2411_14968_gb300 import datagen
+    pool = serving_pool(True)
+    queries = serving_queries(SERVE_QUERIES, pool, native)
+    total_pts = sum(x.shape[0] for x, _ in queries)
+    ctx = native.Context(local)
+    try:
+        # warm-up of both forms on a few queries
+        run_serving(ctx, native, queries[:8], None, "plain", 1, 1)
+        run_serving(ctx, native, queries[:8], None, "persistent", 2, 64)
+        # capacity of the plain one-at-a-time path (back-to-back)
+        _, span_cap, _ = run_serving(ctx, native, queries, None, "plain", 1, 1)
+        cap_qps = len(queries) / span_cap
+        rate = 0.8 * cap_qps
+        arr = datagen.poisson_arrivals(len(queries), rate, SERVE_SEED)
+        res = {}
+        for name, exec_, w, mb in (("plain", "plain", 1, 1), ("batched", "persistent", 2, 64)):
+            lat, span, mean_batch = run_serving(ctx, native, queries, arr, exec_, w, mb)
+            res[name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                         "mean_ms": float(lat.mean()), "points_per_s": total_pts / span,
+                         "queries_per_s": len(queries) / span, "mean_batch_queries": mean_batch}
+        # saturation throughput of the batching loop (all queries at once)
+        _, span_b, mb_sat = run_serving(ctx, native, queries, None, "persistent", 2, 64)
+        res["saturation"] = {"plain_points_per_s": total_pts / span_cap, "batched_points_per_s": total_pts / span_b,
+                             "batched_mean_batch_queries": mb_sat}
+        res["trace"] = (f"{len(queries)} queries of the 10,000-query serving trace (seed {SERVE_SEED}): "
+                        "anticorrelated or independent FP32, N log-uniform in [1e3, 1e6], d uniform in 3..8, "
+                        "Sliced p = clamp(N / 8192, 1, 64); Poisson arrivals at 0.8 x the measured capacity of "
+                        "the plain path")
+        res["offered_queries_per_s"] = rate
+        res["points"] = total_pts
+        return res
+    finally:
+        ctx.close()
+
+
 def gpu_arm(args, rank, world, local):
     import torch
     from paper_2411_14968_gb300 import datagen, native
@@ -185,14 +285,25 @@ def gpu_arm(args, rank, world, local):
     ctx.set_timing(True)
     persistent = {name: native.make_params(exec="persistent", **kw) for name, kw in VARIANTS}
     plain = {name: native.make_params(exec="plain", **kw) for name, kw in VARIANTS}
-    out = torch.empty(N, dtype=torch.int32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    names = [name for name, _ in VARIANTS]
 
-    def step(pmap, acc=None):
+    def step_batched(acc=None):
+        # the four queries as one batch: every local skyline of the four in
+        # one persistent launch, the four merges in a second one
+        res = ctx.skyline_batch([(xt, persistent[nm]) for nm in names])
+        if acc is not None:
+            st = ctx.stats()
+            acc["launches"] += st["launches"]
+            acc["dom_ms"] += st["ms_dom_local"] + st["ms_dom_merge"]
+            acc["stats"].append(st)
+        return {nm: int(r.shape[0]) for nm, r in zip(names, res)}
+
+    def step_each(pmap, acc=None):
         counts = {}
         for name, p in pmap.items():
-            idx = ctx.skyline(xt, params=p, out=out)
+            idx = ctx.skyline(xt, params=p)
             st = ctx.stats()
             counts[name] = int(idx.shape[0])
             if acc is not None:
@@ -201,8 +312,8 @@ def gpu_arm(args, rank, world, local):
                 acc["per_variant"].setdefault(name, []).append(st)
         return counts
 
-    def timed(pmap, k):
-        acc = {"launches": 0, "dom_ms": 0.0, "per_variant": {}}
+    def timed(fn, k):
+        acc = {"launches": 0, "dom_ms": 0.0, "per_variant": {}, "stats": []}
         ms = []
         barrier()
         torch.cuda.synchronize()
@@ -211,7 +322,7 @@ def gpu_arm(args, rank, world, local):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            step(pmap, acc)
+            fn(acc)
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
@@ -219,29 +330,34 @@ def gpu_arm(args, rank, world, local):
         barrier()
         return ms, acc
 
-    # warm-up (also checks that every variant gives the same set: Prop. 1)
+    # warm-up (also checks that every variant and form gives the same set:
+    # Prop. 1)
     ref_counts = None
     for _ in range(max(args.warmup, 3)):
-        c1 = step(persistent)
-        c2 = step(plain)
+        c0 = step_batched()
+        c1 = step_each(persistent)
+        c2 = step_each(plain)
         if ref_counts is None:
             ref_counts = c1
-        assert len(set(c1.values()) | set(c2.values())) == 1, (c1, c2)
+        assert len(set(c0.values()) | set(c1.values()) | set(c2.values())) == 1, (c0, c1, c2)
 
     clocks = ClockSampler(local)
     clocks.start()
-    ms, acc = timed(persistent, args.steps)
+    ms, acc = timed(step_batched, args.steps)
     clk = clocks.stop()
     total_s = max_over_ranks(sum(ms) / 1e3)
     pts_per_step = N * len(VARIANTS)
     value = pts_per_step * args.steps * world / total_s
 
-    # plain form: one launch per partition
-    ms_plain, acc_plain = timed(plain, max(1, args.steps))
+    # one query at a time, every partition of a query in one launch
+    ms_pq, acc_pq = timed(lambda a: step_each(persistent, a), max(1, args.steps))
+    pq_value = pts_per_step * len(ms_pq) * world / max_over_ranks(sum(ms_pq) / 1e3)
+    # plain form: one query at a time, one launch per partition
+    ms_plain, acc_plain = timed(lambda a: step_each(plain, a), max(1, args.steps))
     plain_s = max_over_ranks(sum(ms_plain) / 1e3)
     plain_value = pts_per_step * len(ms_plain) * world / plain_s
 
-    # end to end through the C ABI from pinned host buffers
+    # end to end through the C ABI: pinned host inputs, host outputs
     xh = torch.from_numpy(x).pin_memory().numpy()
     sky_total = sum(ref_counts.values())
     barrier()
@@ -249,8 +365,7 @@ def gpu_arm(args, rank, world, local):
     t0 = time.perf_counter()
     k_e2e = max(1, args.steps)
     for _ in range(k_e2e):
-        for name, p in persistent.items():
-            ctx.skyline(xh, params=p)
+        ctx.skyline_batch([(xh, persistent[nm]) for nm in names])
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e_value = pts_per_step * k_e2e * world / e2e_s
 
@@ -260,18 +375,19 @@ def gpu_arm(args, rank, world, local):
     roof = None
     dom_ms_per_step = acc["dom_ms"] / args.steps
     if wc:
-        tests = sum(wc[name]["local_tests"] + wc[name]["merge_tests"] for name, _ in VARIANTS)
+        tests = sum(wc[name]["local_tests"] + wc[name]["merge_tests"] for name in names)
         achieved = tests * D / (dom_ms_per_step * 1e-3) / 1e12
         peak = args.compare_peak_tcmp
-        roof = {"bound": "alu", "kernel": "k_engine (dominance tiles, local + merge launches)",
+        roof = {"bound": "alu", "kernel": "k_engine (local + merge launches of the batched step)",
                 "achieved": achieved, "peak": peak, "unit": "Tcmp/s", "frac": achieved / peak,
+                "peak_source": "derived: 152 SMs x 64 FP32 compares/clk x 2.07 GHz",
                 "traffic": None, "algorithmic_tests_per_step": tests,
                 "kernel_ms_per_step": dom_ms_per_step,
                 "kernel_share_of_step": dom_ms_per_step / (sum(ms) / len(ms))}
 
-    # per-variant breakdown (medians over the timed steps)
+    # per-variant breakdown of the one-query-at-a-time form (medians)
     per_variant = {}
-    for name, sts in acc["per_variant"].items():
+    for name, sts in acc_pq["per_variant"].items():
         per_variant[name] = {
             "skyline": ref_counts[name],
             "local_union": sts[-1]["local_union"],
@@ -282,6 +398,15 @@ def gpu_arm(args, rank, world, local):
             "ms_dom_merge": statistics.median(s["ms_dom_merge"] for s in sts),
             "ms_phase": [round(statistics.median(s["ms_phase"][i] for s in sts), 4) for i in range(6)],
         }
+    bst = acc["stats"][-1]
+    batched_detail = {"ms_dom_local": bst["ms_dom_local"], "ms_dom_merge": bst["ms_dom_merge"],
+                      "rounds_local": bst["rounds_local"], "rounds_merge": bst["rounds_merge"],
+                      "ms_phase": [round(v, 4) for v in bst["ms_phase"]]}
+    ctx.close()
+
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_leg(native, local)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -296,11 +421,15 @@ def gpu_arm(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded anticorrelated generator; the paper's generator is unstated)",
-            "config": {"workload": WORKLOAD, "points_per_step": pts_per_step, "exec": "persistent",
+            "config": {"workload": WORKLOAD, "points_per_step": pts_per_step,
+                       "exec": "batched: the 4 queries in one call, all local skylines in one persistent launch, "
+                               "all merges in a second",
                        "l2": "flushed between timed steps (256 MB write outside the timed events)",
                        "parallelism": f"replicas x{world}"},
+            "per_query_persistent": {"value": pq_value, "unit": "points/s",
+                                     "ms_per_step": sum(ms_pq) / len(ms_pq)},
             "plain": {"value": plain_value, "unit": "points/s", "ms_per_step": sum(ms_plain) / len(ms_plain),
-                      "speedup_persistent_over_plain": value / plain_value},
+                      "speedup_batched_over_plain": value / plain_value},
             "e2e": {"value": e2e_value, "unit": "points/s",
                     "h2d_bytes_per_step": len(VARIANTS) * N * D * 4,
                     "d2h_bytes_per_step": 4 * sky_total + len(VARIANTS) * 128},
@@ -308,10 +437,11 @@ def gpu_arm(args, rank, world, local):
             "clocks": clk,
             "roofline": roof,
             "cpu_baseline": cpu,
+            "serving": serving,
+            "batched": batched_detail,
             "variants": per_variant,
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -324,6 +454,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     # FP32 compare peak: 152 SMs x 64 compare lanes per SM per clock x 2.07 GHz
     # (the compare-rate probe of the library measures 58.6 per SM per clock)
     ap.add_argument("--compare-peak-tcmp", type=float, default=SM_COUNT * 64 * 2.07e9 / 1e12)

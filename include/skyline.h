@@ -31,7 +31,7 @@
  *  - a context owns its device scratch memory, grows it on demand within
  *    its memory budget and frees it in sky_destroy;
  *  - calls on one context must not run concurrently from several host
- *    threads.
+ *    threads, except sky_submit / sky_poll / sky_wait.
  */
 #ifndef SKYLINE_H_
 #define SKYLINE_H_
@@ -145,6 +145,90 @@ sky_status sky_skyline(sky_ctx* ctx, const float* points, uint64_t n, uint32_t d
 sky_status sky_skyline_ex(sky_ctx* ctx, const float* points, uint64_t n, uint32_t d,
                           const sky_params* params, uint32_t* out_idx, uint64_t* out_count,
                           uint32_t* out_pid, uint8_t* out_stage);
+
+/* One query of a batch (sky_skyline_batch). */
+typedef struct {
+  const float* points;       /* N x d FP32 row-major, host or device */
+  uint64_t n;
+  uint32_t d;
+  const sky_params* params;  /* NULL = defaults */
+  uint32_t* out_idx;         /* capacity >= N, host or device */
+  uint64_t* out_count;       /* host */
+  sky_status status;         /* out: this query's status */
+} sky_query;
+
+/* Runs nq independent skyline queries as one batch: the partitions of all
+   queries are computed in one persistent launch of the dominance engine
+   (Algorithm 2's local phase for every query at once) and the sequential
+   final phases of all queries in a second one, so that many queries of
+   uneven size fill the GPU together.  Each query's result equals what
+   sky_skyline returns for it alone.  Arguments are checked before any work
+   starts: an invalid query fails the whole call (its status says which).
+   Queries asking for SKY_EXEC_PLAIN get their own launches.  Blocks until
+   every result is in its out_idx.  The statistics of the context become
+   the batch's (sums over queries; maxima of round counts). */
+sky_status sky_skyline_batch(sky_ctx* ctx, sky_query* queries, uint32_t nq);
+
+/* ---- serving: a request loop with continuous batching ----------------
+   sky_submit queues a query and returns at once.  Worker threads of the
+   context take queued queries in arrival order into batches whose device
+   memory fits their share of the serving budget, run each batch like
+   sky_skyline_batch on their own stream (the workspaces stay resident
+   between batches), and publish every query's result.  Queries that arrive
+   while a batch is on the GPU join the next batch of the first worker that
+   frees up; with two or more workers one batch's copies and memory-bound
+   stages overlap another's dominance kernel.  Each result equals what
+   sky_skyline returns for the query alone.  sky_submit, sky_poll and
+   sky_wait may be called from several host threads at once. */
+typedef struct {
+  uint32_t struct_size;       /* sizeof(sky_serve_config); set by sky_serve_config_init */
+  uint32_t workers;           /* batches in flight (streams); default 2 */
+  uint32_t max_batch;         /* queries per batch; default 64 */
+  uint64_t mem_budget_bytes;  /* device memory of all workers' workspaces; 0 = half the free memory */
+} sky_serve_config;
+
+typedef struct {
+  double queue_us;            /* submit to the start of its batch */
+  double run_us;              /* start of its batch to its result */
+  double latency_us;          /* submit to result */
+  uint32_t batch_queries;     /* queries in its batch */
+} sky_ticket_info;
+
+void sky_serve_config_init(sky_serve_config* cfg);
+
+/* Device memory (bytes) that one query of this shape takes in a batch: the
+   figure the serving loop admits queries by.  0 if the arguments are
+   invalid. */
+uint64_t sky_query_bytes(uint64_t n, uint32_t d, const sky_params* params);
+
+/* Starts the serving loop of the context (cfg NULL = defaults).  Called
+   implicitly with the defaults by the first sky_submit.  SKY_EBUSY if it
+   is already running. */
+sky_status sky_serve_start(sky_ctx* ctx, const sky_serve_config* cfg);
+
+/* Queues Sky(points) with the given parameters (NULL = defaults); *ticket
+   receives its handle.  points (host or device, N x d FP32 row-major) must
+   stay valid and unchanged until the ticket completes.  Arguments are
+   checked here (SKY_EINVAL); device-side failures are reported by
+   sky_wait. */
+sky_status sky_submit(sky_ctx* ctx, const float* points, uint64_t n, uint32_t d, const sky_params* params,
+                      uint64_t* ticket);
+
+/* SKY_OK if the ticket has completed, SKY_EBUSY if it has not,
+   SKY_ECANCELLED if it is unknown or already collected. */
+sky_status sky_poll(sky_ctx* ctx, uint64_t ticket);
+
+/* Waits up to timeout_us (negative = no limit) for the ticket, copies its
+   |Sky| ascending indices to out_idx (host or device, capacity >= N),
+   *out_count = |Sky|, fills *info if not NULL, and releases the ticket.
+   SKY_EBUSY on timeout (the ticket stays valid), SKY_ECANCELLED for an
+   unknown or collected ticket, else the query's own status. */
+sky_status sky_wait(sky_ctx* ctx, uint64_t ticket, uint32_t* out_idx, uint64_t* out_count, int64_t timeout_us,
+                    sky_ticket_info* info);
+
+/* Runs the queued queries to completion and stops the workers (their
+   workspaces are freed).  Uncollected tickets stay collectable. */
+sky_status sky_serve_stop(sky_ctx* ctx);
 
 /* Statistics of the last completed call. */
 sky_status sky_get_stats(sky_ctx* ctx, sky_stats* out);

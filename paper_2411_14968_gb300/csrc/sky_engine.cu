@@ -723,5 +723,6 @@ cudaError_t engine_run(const SegDesc* segs_dev, u32 nseg, const EngineCfg& cfg, 
 }
 
 u32 engine_max_round_word() { return C_MAXROUND; }
+u32 engine_max_dom_block() { return DBMAX; }
 
 }  // namespace sky

@@ -88,10 +88,12 @@ cudaError_t scan_u8(const u8* in, u32* out, u64 n, bool exclusive, u32* tmp, cud
 // Stable LSD radix sort of (u64 key, u32 value) pairs on key bits [lo_bit,
 // hi_bit).  Input in k[0], v[0]; *out_sel receives the index (0 or 1) of the
 // buffer pair that holds the output.  hist: radix_hist_words(n) u32; tmp:
-// scan_tmp_words(radix_hist_words(n)) u32.
+// scan_tmp_words(radix_hist_words(n)) u32.  With n_dev the element count is
+// min(n, *n_dev), read on the device (n is the capacity the grids are sized
+// for), so no host round trip is needed.
 size_t radix_hist_words(u64 n);
 cudaError_t radix_sort(u64* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32* hist, u32* tmp,
-                       cudaStream_t st, int* out_sel);
+                       cudaStream_t st, int* out_sel, const u32* n_dev = nullptr);
 
 // ---------------------------------------------------------------- prep (sky_prep.cu)
 struct PrepArgs {
@@ -150,13 +152,16 @@ cudaError_t launch_compact_u(const u8* alive, const u32* excl, u64 n, int d, con
 // useg[s] = offset of u_s in u (P + 1 entries); total = device pointer to |u|.
 cudaError_t launch_useg(const u32* seg_off, u32 P, const u32* excl, u64 n, const u32* total, u32* useg,
                         cudaStream_t st);
-cudaError_t launch_gather_u(const u32* order, u64 n, int d, const float* upts, const uint4* uhc,
+// u in score order: entry r of the merge array is u[order[r]], for r below
+// n (capacity) and *n_dev (if given).
+cudaError_t launch_gather_u(const u32* order, u64 n, const u32* n_dev, int d, const float* upts, const uint4* uhc,
                             const float* uscore, const u32* upos, float* mpts, uint4* mhc, float* mscore,
                             u32* mpos, cudaStream_t st);
-// Points dead in a merge array: their sorted-position flag is cleared and,
-// if no stage was recorded yet, stage `code` is recorded.
-cudaError_t launch_scatter_alive(const u8* malive, const u32* mpos, u64 n, u8* alive, u8* stage_s,
-                                 u8 code, cudaStream_t st);
+// Points dead in a merge array (entries below n and *n_dev if given): their
+// sorted-position flag is cleared and, if no stage was recorded yet, stage
+// `code` is recorded.
+cudaError_t launch_scatter_alive(const u8* malive, const u32* mpos, u64 n, const u32* n_dev, u8* alive,
+                                 u8* stage_s, u8 code, cudaStream_t st);
 // Points dead (alive == 0) with no stage recorded get `code`.
 cudaError_t launch_stamp_stage(const u8* alive, u64 n, u8* stage_s, u8 code, cudaStream_t st);
 // Output mask in input order; a point with no stage recorded is in the
@@ -218,6 +223,8 @@ constexpr int ENGINE_CTL_WORDS = 16;
 u64 engine_tile_capacity(u64 total_points, u32 nseg);
 // Control word that receives the largest round count of a launch.
 u32 engine_max_round_word();
+// Largest dominator block (points) the engine stages in shared memory.
+u32 engine_max_dom_block();
 
 // Local skylines of segs[0..nseg) in one cooperative launch (grid = the
 // co-resident capacity).  Kills dominated points (alive = 0) and leaves each

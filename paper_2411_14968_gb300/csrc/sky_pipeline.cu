@@ -1,0 +1,848 @@
+// Host-side orchestration of Algorithm 2 (Section 3) with the optimisations
+// of Sections 3.2 (Grid Filtering), 4.1 (Sorted representatives) and 4.2
+// (NoSeq), over a batch of independent queries.  Every step runs in the
+// kernels of sky_prep.cu, sky_prims.cu, sky_dom.cu and sky_engine.cu; the
+// host sizes buffers, launches, and copies the results once at the end.
+//
+// Batching: the partitions of every query of a batch are segments of one
+// persistent engine launch (the local phase), and the merge inputs of every
+// query with a sequential final phase are segments of a second one, so the
+// uneven work of many queries fills the GPU together.  There is no host
+// round trip between the first launch and the final copy of the counts:
+// sizes that are only known on the device (|u|) are read by the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include "sky_pipeline.cuh"
+
+namespace sky {
+
+namespace {
+
+// Bump allocator over one scratch block; sizes are rounded to 256 bytes.
+struct Carve {
+  char* base;
+  size_t off;
+  explicit Carve(char* b, size_t start = 0) : base(b), off(start) {}
+  template <class T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~(size_t)255;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += bytes ? bytes : 256;
+    return p;
+  }
+};
+
+struct Plan {
+  u64 n = 0;
+  int d = 0, V = 1;
+  int scheme = SCHEME_NONE;
+  u32 P = 1;
+  u32 slices[8] = {1, 1, 1, 1, 1, 1, 1, 1};
+  int normalize = 0, slice_dim = 0;
+  u64 seed = 0;
+  bool grid_filter = false;
+  int rep = 0;
+  u32 k = 1;
+  int merge = 0;
+  int exec = 0;
+  EngineCfg cfg{};
+  int pid_bits = 0;
+  bool x_on_host = false;
+};
+
+// Per-query device buffers.
+struct Bufs {
+  float* X;
+  u64* keys[2];
+  u32* vals[2];
+  u32* head;
+  float* pts;
+  uint4* hc;
+  float* score;
+  u32* orig;
+  u32* spid;
+  u8* alive;
+  u8* stage_s;
+  u32* seg_off;
+  u32* scan_tmp;
+  u32* hist;
+  float* win;
+  uint4* whc;
+  u32* dpos;
+  uint4* dhc;
+  float* upts;
+  uint4* uhc;
+  float* uscore;
+  u32* upos;
+  u32* useg;
+  float* mpts;
+  uint4* mhc;
+  float* mscore;
+  u32* mpos;
+  u8* malive;
+  u8* ualive;
+  u32* words;  // err, colmax[8], counters
+  u8* clos;
+  u8* dropped;
+  float* rep_pts;
+  u8* rep_alive;
+  float* kept_pts;
+  u32* rep_excl;
+  float* ang_table;
+  u8* mask;
+  u32* excl;
+  u32* out_dev;
+  u32* gcnt;
+  u32* gpre;
+};
+
+// Engine state shared by the queries of a batch.
+struct BatchBufs {
+  SegDesc* segs;    // local-phase segments of every query
+  SegDesc* msegs;   // merge segments (one per query with a sequential final phase)
+  SegState* st;
+  u32* done_round;
+  u32* tdoneA;
+  u32* tdoneB;
+  u64 tcap;
+  u32* ctl;
+};
+
+// word slots of Bufs::words
+enum { W_ERR = 0, W_COLMAX = 1, W_GRID_DROPPED = 9, W_KEPT = 10, W_NU = 11, W_SKY = 12, W_MAXROUND_LOCAL = 13,
+       W_MAXROUND_MERGE = 14, W_HIST = 16, W_WORDS = 32 };
+
+size_t layout(const Plan& pl, u32 ang_words, Carve& c, Bufs* b) {
+  const size_t start = c.off;
+  const u64 n = pl.n ? pl.n : 1;
+  const u64 P = pl.P;
+  const u64 V = pl.V;
+  const u64 nrep = (pl.rep ? P * pl.k : 1);
+  b->X = c.take<float>(pl.x_on_host ? n * pl.d : 1);
+  b->keys[0] = c.take<u64>(n);
+  b->keys[1] = c.take<u64>(n);
+  b->vals[0] = c.take<u32>(n);
+  b->vals[1] = c.take<u32>(n);
+  b->head = c.take<u32>(n);
+  b->pts = c.take<float>(n * 4 * V);
+  b->hc = c.take<uint4>(n);
+  b->score = c.take<float>(n);
+  b->orig = c.take<u32>(n);
+  b->spid = c.take<u32>(n);
+  b->alive = c.take<u8>(n);
+  b->stage_s = c.take<u8>(n);
+  b->seg_off = c.take<u32>(P + 1);
+  size_t scan_words = scan_tmp_words(std::max<u64>({(u64)radix_hist_words(n), n, P + 1, nrep}));
+  b->scan_tmp = c.take<u32>(scan_words);
+  b->hist = c.take<u32>(radix_hist_words(n));
+  b->win = c.take<float>(n * 4 * V);
+  b->whc = c.take<uint4>(n);
+  b->dpos = c.take<u32>(n);
+  b->dhc = c.take<uint4>(n);
+  b->upts = c.take<float>(n * 4 * V);
+  b->uhc = c.take<uint4>(n);
+  b->uscore = c.take<float>(n);
+  b->upos = c.take<u32>(n);
+  b->useg = c.take<u32>(P + 1);
+  b->mpts = c.take<float>(n * 4 * V);
+  b->mhc = c.take<uint4>(n);
+  b->mscore = c.take<float>(n);
+  b->mpos = c.take<u32>(n);
+  b->malive = c.take<u8>(n);
+  b->ualive = c.take<u8>(n);
+  b->words = c.take<u32>(W_WORDS);
+  b->clos = c.take<u8>(P);
+  b->dropped = c.take<u8>(P);
+  b->rep_pts = c.take<float>(nrep * 4 * V);
+  b->rep_alive = c.take<u8>(nrep);
+  b->kept_pts = c.take<float>(nrep * 4 * V);
+  b->rep_excl = c.take<u32>(nrep);
+  b->ang_table = c.take<float>(ang_words ? ang_words : 1);
+  b->mask = c.take<u8>(n);
+  b->excl = c.take<u32>(n);
+  b->out_dev = c.take<u32>(n);
+  b->gcnt = c.take<u32>(P + 1);
+  b->gpre = c.take<u32>(P + 1);
+  return c.off - start;
+}
+
+void layout_batch(u64 total_pts, u32 total_segs, u32 nmerge, Carve& c, BatchBufs* bb) {
+  const u32 nseg = std::max(std::max(total_segs, nmerge), 1u);
+  bb->segs = c.take<SegDesc>(std::max(total_segs, 1u));
+  bb->msegs = c.take<SegDesc>(std::max(nmerge, 1u));
+  bb->st = c.take<SegState>(2 * (size_t)nseg);
+  bb->done_round = c.take<u32>(nseg);
+  bb->tcap = engine_tile_capacity(std::max<u64>(total_pts, 1), nseg);
+  bb->tdoneA = c.take<u32>(bb->tcap);
+  bb->tdoneB = c.take<u32>(bb->tcap);
+  bb->ctl = c.take<u32>(ENGINE_CTL_WORDS);
+}
+
+int bits_for(u64 v) {  // bits needed to represent values in [0, v)
+  int b = 0;
+  while (b < 64 && (1ull << b) < v) ++b;
+  return b;
+}
+
+// Checks the arguments of one query and derives its plan; msg receives the
+// reason of a failure.
+sky_status validate(const float* points, u64 n, u32 d, const sky_params* pa, Plan* pl, std::string* msg) {
+  auto bad = [&](const char* m) {
+    *msg = m;
+    return SKY_EINVAL;
+  };
+  if (d < 1 || d > 8) return bad("d must be in 1..8");
+  if (n >= (1ull << 32) - 1) return bad("N must be below 2^32 - 1");
+  if (n > 0 && !points) return bad("points is NULL");
+  sky_params def;
+  sky_params_init(&def);
+  const sky_params& p = pa ? *pa : def;
+  if (pa && pa->struct_size != sizeof(sky_params)) return bad("sky_params.struct_size mismatch");
+  pl->n = n;
+  pl->d = (int)d;
+  pl->V = vec_of((int)d);
+  pl->scheme = (int)p.scheme;
+  pl->normalize = p.normalize ? 1 : 0;
+  pl->seed = p.seed;
+  pl->rep = p.rep == SKY_REP_SORTED ? 1 : 0;
+  if (p.rep != SKY_REP_NONE && p.rep != SKY_REP_SORTED) return bad("unknown rep mode");
+  pl->k = p.reps_per_partition ? p.reps_per_partition : 1;
+  if (p.merge != SKY_MERGE_SEQUENTIAL && p.merge != SKY_MERGE_NOSEQ) return bad("unknown merge");
+  pl->merge = (int)p.merge;
+  if (p.exec != SKY_EXEC_PERSISTENT && p.exec != SKY_EXEC_PLAIN) return bad("unknown exec");
+  pl->exec = (int)p.exec;
+  u64 P = 1;
+  switch (p.scheme) {
+    case SKY_GRID:
+      for (u32 a = 0; a < d; ++a) {
+        if (p.slices[a] < 1) return bad("Grid slices must be >= 1");
+        P *= p.slices[a];
+        if (P > (1u << 20)) return bad("Grid cell count above 2^20");
+        pl->slices[a] = p.slices[a];
+      }
+      pl->grid_filter = p.grid_filter != 0;
+      break;
+    case SKY_ANGULAR:
+      for (u32 a = 0; a + 1 < d; ++a) {
+        if (p.slices[a] < 1) return bad("Angular slices must be >= 1");
+        P *= p.slices[a];
+        if (P > (1u << 20)) return bad("Angular partition count above 2^20");
+        pl->slices[a] = p.slices[a];
+      }
+      break;
+    case SKY_RANDOM:
+    case SKY_SLICED:
+      P = p.num_partitions ? p.num_partitions : 1;
+      if (P > (1u << 20)) return bad("partition count above 2^20");
+      if (n > 0 && P > n) P = n;
+      if (p.scheme == SKY_SLICED) {
+        if (p.slice_dim >= d) return bad("slice_dim must be < d");
+        pl->slice_dim = (int)p.slice_dim;
+      }
+      break;
+    case SKY_NONE:
+      P = 1;
+      break;
+    default:
+      return bad("unknown partitioning scheme");
+  }
+  pl->P = (u32)P;
+  if (pl->rep && (u64)pl->P * pl->k > (1u << 22)) return bad("too many representatives");
+  pl->pid_bits = bits_for(P);
+  pl->cfg.chunk_min = p.chunk_min ? p.chunk_min : 4096;
+  pl->cfg.chunk_max = p.chunk_max ? p.chunk_max : 65536;
+  if (pl->cfg.chunk_max < pl->cfg.chunk_min) pl->cfg.chunk_max = pl->cfg.chunk_min;
+  pl->cfg.alpha_x4 = p.chunk_alpha_x4 ? p.chunk_alpha_x4 : 8;
+  pl->cfg.dom_block = p.dom_block ? p.dom_block : 1024;
+  if (pl->cfg.dom_block % 32) return bad("dom_block must be a multiple of 32");
+  if (pl->cfg.dom_block > engine_max_dom_block()) return bad("dom_block above the engine's maximum");
+  if (pl->cfg.chunk_min > (1u << 24) || pl->cfg.chunk_max > (1u << 24)) return bad("chunk too large");
+  return SKY_OK;
+}
+
+// Angular thresholds tan^2(k pi / (2 m)), k = 1..m-1, evaluated in double
+// and rounded to FP32 (Section 3.3 evaluated without device transcendentals).
+void angular_table(const Plan& pl, std::vector<float>* tab, u32* off) {
+  tab->clear();
+  const double pi = 3.14159265358979323846;
+  for (int a = 0; a + 1 < pl.d; ++a) {
+    off[a] = (u32)tab->size();
+    u32 m = pl.slices[a];
+    for (u32 k = 1; k < m; ++k) {
+      double t = tan((double)k * pi / (2.0 * (double)m));
+      tab->push_back((float)(t * t));
+    }
+  }
+  if (tab->empty()) tab->push_back(0.0f);
+}
+
+// Everything the pipeline keeps about one query between its stages.
+struct Work {
+  Runner::Query* q;
+  Plan pl;
+  std::vector<float> tab;
+  u32 ang_off[8] = {0};
+  Bufs b;
+  const float* X = nullptr;   // device copy of the input
+  const u8* dropped = nullptr;
+  u32 seg_base = 0;          // first local segment in the batch array
+  int mseg = -1;             // merge segment, or -1
+  bool out_dev = false;
+  u32 words[W_WORDS] = {0};
+};
+
+#define CK(expr)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (expr);                                                           \
+    if (e_ != cudaSuccess) return fail(SKY_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+}  // namespace
+
+sky_status validate_query(const float* points, u64 n, u32 d, const sky_params* params, std::string* msg) {
+  Plan pl;
+  return validate(points, n, d, params, &pl, msg);
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+Runner::~Runner() {
+  if (ws_ || pinned_ || ev_[0]) {
+    cudaSetDevice(device);
+    cudaStreamSynchronize(stream);
+  }
+  if (ws_) cudaFree(ws_);
+  if (pinned_) cudaFreeHost(pinned_);
+  for (auto& e : ev_)
+    if (e) cudaEventDestroy(e);
+  if (gate_ev_) cudaEventDestroy(gate_ev_);
+}
+
+sky_status Runner::init(int dev, size_t mem_budget) {
+  device = dev;
+  budget = mem_budget;
+  if (cudaSetDevice(dev) != cudaSuccess) return SKY_ECUDA;
+  for (auto& e : ev_)
+    if (cudaEventCreate(&e) != cudaSuccess) return SKY_ECUDA;
+  if (cudaEventCreateWithFlags(&gate_ev_, cudaEventDisableTiming) != cudaSuccess) return SKY_ECUDA;
+  return ensure_pinned(64);
+}
+
+void Runner::release() {
+  if (ws_) {
+    cudaSetDevice(device);
+    cudaStreamSynchronize(stream);
+    cudaFree(ws_);
+  }
+  ws_ = nullptr;
+  ws_size_ = 0;
+}
+
+sky_status Runner::fail(sky_status s, const std::string& msg) {
+  last_error = msg;
+  return s;
+}
+
+sky_status Runner::ensure_ws(size_t bytes) {
+  if (bytes <= ws_size_) return SKY_OK;
+  if (budget && bytes > budget)
+    return fail(SKY_ENOMEM, "scratch memory of " + std::to_string(bytes) + " bytes exceeds the budget");
+  release();
+  size_t grow = bytes + bytes / 8;
+  if (budget && grow > budget) grow = bytes;
+  cudaError_t e = cudaMalloc(&ws_, grow);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ws_ = nullptr;
+    return fail(SKY_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  ws_size_ = grow;
+  return SKY_OK;
+}
+
+sky_status Runner::ensure_pinned(size_t words) {
+  if (words <= pinned_words_) return SKY_OK;
+  if (pinned_) {
+    cudaStreamSynchronize(stream);
+    cudaFreeHost(pinned_);
+    pinned_ = nullptr;
+    pinned_words_ = 0;
+  }
+  if (cudaMallocHost(&pinned_, words * sizeof(u32)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SKY_ENOMEM, "cudaMallocHost failed");
+  }
+  pinned_words_ = words;
+  return SKY_OK;
+}
+
+void Runner::record(int i) {
+  if (timing) cudaEventRecord(ev_[i], stream);
+}
+
+size_t Runner::query_bytes(u64 n, u32 d, const sky_params* params) {
+  Plan pl;
+  std::string msg;
+  if (validate(reinterpret_cast<const float*>(1), n, d, params, &pl, &msg) != SKY_OK) return 0;
+  pl.x_on_host = true;
+  std::vector<float> tab;
+  u32 off[8];
+  if (pl.scheme == SCHEME_ANGULAR) angular_table(pl, &tab, off);
+  Bufs b;
+  Carve c(nullptr);
+  size_t q = layout(pl, (u32)std::max<size_t>(tab.size(), 1), c, &b);
+  Carve c2(nullptr);
+  BatchBufs bb;
+  layout_batch(n, pl.P, 1, c2, &bb);
+  return q + c2.off;
+}
+
+sky_status Runner::run(Query* queries, u32 nq) {
+  const u64 launches0 = launch_counter();
+  memset(&stats, 0, sizeof(stats));
+  CK(cudaSetDevice(device));
+  std::vector<Work> ws(nq);
+  // ---- validate and size
+  u64 total_pts = 0;
+  u32 total_segs = 0, nmerge = 0;
+  std::vector<size_t> offs(nq);
+  size_t need = 0;
+  for (u32 i = 0; i < nq; ++i) {
+    Work& w = ws[i];
+    Query& q = queries[i];
+    w.q = &q;
+    q.status = SKY_OK;
+    memset(&q.stats, 0, sizeof(q.stats));
+    std::string msg;
+    sky_status s = validate(q.points, q.n, q.d, q.params, &w.pl, &msg);
+    if (s == SKY_OK && !q.out_count) {
+      s = SKY_EINVAL;
+      msg = "out_count is NULL";
+    }
+    if (s == SKY_OK && q.n > 0 && !q.out_idx) {
+      s = SKY_EINVAL;
+      msg = "out_idx is NULL";
+    }
+    if (s != SKY_OK) {
+      q.status = s;
+      return fail(s, nq > 1 ? "query " + std::to_string(i) + ": " + msg : msg);
+    }
+    q.stats.n = q.n;
+    q.stats.d = q.d;
+    q.stats.partitions = w.pl.P;
+    if (q.n == 0) continue;
+    w.pl.x_on_host = !is_device_ptr(q.points);
+    w.out_dev = is_device_ptr(q.out_idx);
+    if (w.pl.scheme == SCHEME_ANGULAR) angular_table(w.pl, &w.tab, w.ang_off);
+    Carve c(nullptr, need);
+    offs[i] = need;
+    need += layout(w.pl, (u32)std::max<size_t>(w.tab.size(), 1), c, &w.b);
+    total_pts += q.n;
+    total_segs += w.pl.P;
+    if (w.pl.P > 1 && w.pl.merge == SKY_MERGE_SEQUENTIAL) ++nmerge;
+  }
+  for (u32 i = 0; i < nq; ++i)
+    if (queries[i].n == 0) *queries[i].out_count = 0;
+  if (total_pts == 0) return SKY_OK;
+  BatchBufs bb;
+  {
+    Carve c(nullptr, need);
+    layout_batch(total_pts, total_segs, nmerge, c, &bb);
+    need = c.off;
+  }
+  sky_status s = ensure_ws(need);
+  if (s != SKY_OK) return s;
+  s = ensure_pinned((size_t)nq * W_WORDS);
+  if (s != SKY_OK) return s;
+  {
+    size_t batch_off = 0;
+    for (u32 i = 0; i < nq; ++i) {
+      Work& w = ws[i];
+      if (w.q->n == 0) continue;
+      Carve c(ws_, offs[i]);
+      layout(w.pl, (u32)std::max<size_t>(w.tab.size(), 1), c, &w.b);
+      batch_off = std::max(batch_off, c.off);
+    }
+    Carve c(ws_, batch_off);
+    layout_batch(total_pts, total_segs, nmerge, c, &bb);
+  }
+  const cudaStream_t st = stream;
+
+  // Segment order: persistent queries first (one launch covers them), then
+  // queries that ask for one launch per partition.
+  {
+    u32 sb = 0, mb = 0;
+    for (int pass = 0; pass < 2; ++pass)
+      for (auto& w : ws) {
+        if (w.q->n == 0 || (w.pl.exec == SKY_EXEC_PLAIN) != (pass == 1)) continue;
+        w.seg_base = sb;
+        sb += w.pl.P;
+        if (w.pl.P > 1 && w.pl.merge == SKY_MERGE_SEQUENTIAL) w.mseg = (int)mb++;
+      }
+  }
+
+  record(0);
+  for (auto& w : ws) {
+    if (w.q->n == 0) continue;
+    w.X = w.q->points;
+    if (w.pl.x_on_host) {
+      CK(cudaMemcpyAsync(w.b.X, w.q->points, w.q->n * w.q->d * sizeof(float), cudaMemcpyHostToDevice, st));
+      w.X = w.b.X;
+    }
+  }
+  record(1);
+
+  // ---- Partition(r, p): keys, sort, gather (Algorithm 2 first phase)
+  for (auto& w : ws) {
+    if (w.q->n == 0) continue;
+    const Plan& pl = w.pl;
+    Bufs& b = w.b;
+    const u64 n = pl.n;
+    const int D = pl.d;
+    u32* err = b.words + W_ERR;
+    CK(cudaMemsetAsync(b.words, 0, W_WORDS * sizeof(u32), st));
+    CK(cudaMemsetAsync(b.stage_s, 0, n, st));
+    PrepArgs pr{};
+    pr.X = w.X;
+    pr.n = n;
+    pr.scheme = pl.scheme;
+    pr.normalize = pl.normalize && (pl.scheme == SCHEME_GRID || pl.scheme == SCHEME_ANGULAR);
+    pr.slice_dim = pl.slice_dim;
+    pr.seed = pl.seed;
+    for (int a = 0; a < 8; ++a) pr.slices[a] = pl.slices[a];
+    pr.colmax = b.words + W_COLMAX;
+    if (pl.scheme == SCHEME_ANGULAR) {
+      CK(cudaMemcpyAsync(b.ang_table, w.tab.data(), w.tab.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+      for (int a = 0; a < 8; ++a) pr.ang_off[a] = w.ang_off[a];
+    }
+    pr.ang_table = b.ang_table;
+    pr.keys = b.keys[0];
+    pr.vals = b.vals[0];
+    pr.err = err;
+    if (pr.normalize) CK(launch_colmax(w.X, n, D, b.words + W_COLMAX, err, st));
+    CK(launch_prep(pr, D, st));
+    int sel = 0;
+    if (pl.scheme == SCHEME_RANDOM || pl.scheme == SCHEME_SLICED) {
+      CK(radix_sort(b.keys, b.vals, n, 0, 64, b.hist, b.scan_tmp, st, &sel));
+      const u32* run_start = nullptr;
+      if (pl.scheme == SCHEME_SLICED) {
+        CK(launch_run_heads(b.keys[sel], n, b.head, st));
+        CK(scan_u32(b.head, b.head, n, false, true, b.scan_tmp, st));
+        run_start = b.head;
+      }
+      // rekey into the other buffer pair, then sort by (partition, score)
+      CK(launch_rekey(w.X, n, D, b.vals[sel], run_start, pl.P, b.keys[sel ^ 1], b.vals[sel ^ 1], st));
+      u64* k2[2] = {b.keys[sel ^ 1], b.keys[sel]};
+      u32* v2[2] = {b.vals[sel ^ 1], b.vals[sel]};
+      int sel2 = 0;
+      CK(radix_sort(k2, v2, n, 0, 32 + pl.pid_bits, b.hist, b.scan_tmp, st, &sel2));
+      sel = sel2 == 0 ? (sel ^ 1) : sel;
+    } else {
+      int hi = (pl.scheme == SCHEME_NONE) ? 32 : 32 + pl.pid_bits;
+      CK(radix_sort(b.keys, b.vals, n, 0, hi, b.hist, b.scan_tmp, st, &sel));
+    }
+    GatherArgs ga{};
+    ga.X = w.X;
+    ga.n = n;
+    ga.keys = b.keys[sel];
+    ga.vals = b.vals[sel];
+    ga.P = pl.P;
+    ga.pts = b.pts;
+    ga.hc = b.hc;
+    ga.score = b.score;
+    ga.orig = b.orig;
+    ga.spid = b.spid;
+    ga.alive = b.alive;
+    ga.seg_off = b.seg_off;
+    CK(launch_gather(ga, D, st));
+  }
+  record(2);
+
+  // ---- Grid Filtering (3.2), Sorted representatives (4.1), segments
+  for (auto& w : ws) {
+    if (w.q->n == 0) continue;
+    const Plan& pl = w.pl;
+    Bufs& b = w.b;
+    const u64 n = pl.n;
+    const int D = pl.d;
+    const u32 P = pl.P;
+    if (pl.scheme == SCHEME_GRID && pl.grid_filter) {
+      GridDims gd;
+      for (int a = 0; a < 8; ++a) gd.m[a] = pl.slices[a];
+      CK(launch_grid_filter(b.seg_off, b.spid, n, D, gd, P, b.clos, b.dropped, b.alive, b.stage_s,
+                            b.words + W_GRID_DROPPED, st));
+      w.dropped = b.dropped;
+    }
+    if (pl.rep) {
+      u32 nrep = P * pl.k;
+      CK(launch_rep_select(b.seg_off, P, pl.k, w.dropped, b.pts, D, b.rep_pts, b.rep_alive, st));
+      // R = Sky(reps): dominated representatives are discarded first
+      CK(launch_relative(b.rep_pts, b.rep_alive, nrep, b.rep_pts, nrep, nullptr, D, st));
+      CK(scan_u8(b.rep_alive, b.rep_excl, nrep, true, b.scan_tmp, st));
+      CK(cudaMemcpyAsync(b.words + W_KEPT, b.scan_tmp + scan_total_index(nrep), sizeof(u32),
+                         cudaMemcpyDeviceToDevice, st));
+      CK(launch_compact_reps(b.rep_alive, b.rep_excl, nrep, D, b.rep_pts, b.kept_pts, st));
+      CK(launch_relative(b.pts, b.alive, n, b.kept_pts, 0, b.words + W_KEPT, D, st));
+      CK(launch_stamp_stage(b.alive, n, b.stage_s, ST_REP, st));
+    }
+    SegArrays sa{b.pts, b.hc, b.score, b.alive, b.win, b.whc, b.dpos, b.dhc};
+    CK(launch_build_segs(b.seg_off, P, w.dropped, sa, D, bb.segs + w.seg_base, st));
+  }
+  record(3);
+
+  // ---- ComputeLocalSet: u_i = Sky(r_i) for every partition of every query
+  EngineWork ew;
+  ew.st = bb.st;
+  ew.done_round = bb.done_round;
+  ew.tdoneA = bb.tdoneA;
+  ew.tdoneB = bb.tdoneB;
+  ew.tcap = bb.tcap;
+  ew.ctl = bb.ctl;
+  const u32* maxround = bb.ctl + engine_max_round_word();
+  auto engine = [&](const SegDesc* segs, u32 nseg, const EngineCfg& cfg, u32* err, u32* round_dst) -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(bb.tdoneA, 0, bb.tcap * sizeof(u32), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bb.tdoneB, 0, bb.tcap * sizeof(u32), st);
+    if (e != cudaSuccess) return e;
+    if (gate) {
+      std::lock_guard<std::mutex> g(gate->mu);
+      if (gate->last) e = cudaStreamWaitEvent(st, gate->last, 0);
+      if (e == cudaSuccess) e = engine_run(segs, nseg, cfg, ew, err, st);
+      if (e == cudaSuccess) e = cudaEventRecord(gate_ev_, st);
+      if (e == cudaSuccess) gate->last = gate_ev_;
+    } else {
+      e = engine_run(segs, nseg, cfg, ew, err, st);
+    }
+    if (e == cudaSuccess) e = launch_fold_max(maxround, round_dst, st);
+    return e;
+  };
+  // the error word and round counter of a shared launch go to the first
+  // query of the launch; the host folds them into every query of it
+  Work* first_persistent = nullptr;
+  u32 persistent_segs = 0;
+  for (auto& w : ws) {
+    if (w.q->n == 0 || w.pl.exec == SKY_EXEC_PLAIN) continue;
+    if (!first_persistent) first_persistent = &w;
+    persistent_segs += w.pl.P;
+  }
+  record(8);
+  if (first_persistent) {
+    // the engine's chunk policy of a shared launch is the first query's
+    CK(engine(bb.segs, persistent_segs, first_persistent->pl.cfg, first_persistent->b.words + W_ERR,
+              first_persistent->b.words + W_MAXROUND_LOCAL));
+  }
+  for (auto& w : ws) {
+    if (w.q->n == 0 || w.pl.exec != SKY_EXEC_PLAIN) continue;
+    for (u32 p = 0; p < w.pl.P; ++p)
+      CK(engine(bb.segs + w.seg_base + p, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_LOCAL));
+  }
+  record(9);
+  for (auto& w : ws) {
+    if (w.q->n == 0) continue;
+    CK(launch_stamp_stage(w.b.alive, w.pl.n, w.b.stage_s, ST_LOCAL, st));
+  }
+  record(4);
+
+  // ---- final phase over u (sequential Sky(u), or NoSeq, Section 4.2)
+  for (auto& w : ws) {
+    if (w.q->n == 0 || w.pl.P <= 1) continue;
+    const Plan& pl = w.pl;
+    Bufs& b = w.b;
+    const u64 n = pl.n;
+    const int D = pl.d;
+    const u32* nu_dev = b.words + W_NU;
+    CK(scan_u8(b.alive, b.excl, n, true, b.scan_tmp, st));
+    CK(cudaMemcpyAsync(b.words + W_NU, b.scan_tmp + scan_total_index(n), sizeof(u32), cudaMemcpyDeviceToDevice,
+                       st));
+    const bool seq = pl.merge == SKY_MERGE_SEQUENTIAL;
+    CK(launch_compact_u(b.alive, b.excl, n, D, b.pts, b.hc, b.score, b.spid, b.upts, b.uhc, b.uscore, b.upos,
+                        nullptr, seq ? b.keys[0] : nullptr, seq ? b.vals[0] : nullptr, st));
+    if (seq) {
+      // sort u by score; |u| is read on the device
+      int msel = 0;
+      CK(radix_sort(b.keys, b.vals, n, 0, 32, b.hist, b.scan_tmp, st, &msel, nu_dev));
+      CK(launch_gather_u(b.vals[msel], n, nu_dev, D, b.upts, b.uhc, b.uscore, b.upos, b.mpts, b.mhc, b.mscore,
+                         b.mpos, st));
+      CK(cudaMemsetAsync(b.malive, 1, n, st));
+      SegArrays ma{b.mpts, b.mhc, b.mscore, b.malive, b.win, b.whc, b.dpos, b.dhc};
+      CK(launch_build_one_seg(ma, nu_dev, D, bb.msegs + w.mseg, st));
+    } else {
+      CK(launch_useg(b.seg_off, pl.P, b.excl, n, nu_dev, b.useg, st));
+      CK(cudaMemsetAsync(b.ualive, 1, n, st));
+      NoSeqArgs na{};
+      na.upts = reinterpret_cast<const float4*>(b.upts);
+      na.uscore = b.uscore;
+      na.useg = b.useg;
+      na.ualive = b.ualive;
+      na.P = pl.P;
+      na.scheme = pl.scheme;
+      na.d = D;
+      for (int a = 0; a < 8; ++a) na.gd.m[a] = pl.slices[a];
+      na.dom_block = pl.cfg.dom_block;
+      // keep the item count within 32 bits
+      while (((n / 64 + pl.P + 1) * (n / na.dom_block + 1)) >= (1ull << 31)) na.dom_block *= 2;
+      CK(launch_noseq(na, b.gcnt, b.gpre, b.scan_tmp, nu_dev, bb.ctl, st));
+      // u is a prefix of the sorted positions' survivors: upos maps back
+      CK(launch_scatter_alive(b.ualive, b.upos, n, nu_dev, b.alive, b.stage_s, ST_MERGE, st));
+    }
+  }
+  record(10);
+  {
+    Work* first = nullptr;
+    u32 cnt = 0;
+    for (auto& w : ws)
+      if (w.mseg >= 0 && w.pl.exec != SKY_EXEC_PLAIN) {
+        if (!first) first = &w;
+        ++cnt;
+      }
+    if (first) CK(engine(bb.msegs, cnt, first->pl.cfg, first->b.words + W_ERR, first->b.words + W_MAXROUND_MERGE));
+    for (auto& w : ws)
+      if (w.mseg >= 0 && w.pl.exec == SKY_EXEC_PLAIN)
+        CK(engine(bb.msegs + w.mseg, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_MERGE));
+  }
+  record(11);
+  for (auto& w : ws) {
+    if (w.mseg < 0) continue;
+    Bufs& b = w.b;
+    CK(launch_scatter_alive(b.malive, b.mpos, w.pl.n, b.words + W_NU, b.alive, b.stage_s, ST_MERGE, st));
+  }
+  record(5);
+
+  // ---- output: ascending indices of Sky(r)
+  for (u32 i = 0; i < nq; ++i) {
+    Work& w = ws[i];
+    if (w.q->n == 0) continue;
+    Bufs& b = w.b;
+    const u64 n = w.pl.n;
+    u32* out_pid = w.q->out_pid;
+    u8* out_stage = w.q->out_stage;
+    CK(launch_output(b.stage_s, b.orig, b.spid, n, b.mask,
+                     out_stage && is_device_ptr(out_stage) ? out_stage : nullptr,
+                     out_pid && is_device_ptr(out_pid) ? out_pid : nullptr, st));
+    CK(scan_u8(b.mask, b.excl, n, true, b.scan_tmp, st));
+    CK(cudaMemcpyAsync(b.words + W_SKY, b.scan_tmp + scan_total_index(n), sizeof(u32), cudaMemcpyDeviceToDevice,
+                       st));
+    CK(launch_compact_idx(b.mask, b.excl, n, w.out_dev ? w.q->out_idx : b.out_dev, st));
+    CK(launch_stage_hist(b.stage_s, n, b.words + W_HIST, st));
+  }
+  record(6);
+  for (u32 i = 0; i < nq; ++i) {
+    Work& w = ws[i];
+    if (w.q->n == 0) continue;
+    CK(cudaMemcpyAsync(pinned_ + (size_t)i * W_WORDS, w.b.words, W_WORDS * sizeof(u32), cudaMemcpyDeviceToHost,
+                       st));
+  }
+  CK(cudaStreamSynchronize(st));
+  // the error word and round counts of a shared engine launch were written
+  // to its first query: every query of the launch shares them
+  u32 shared_err = 0, shared_round_local = 0, shared_round_merge = 0;
+  for (u32 i = 0; i < nq; ++i) {
+    Work& w = ws[i];
+    if (w.q->n == 0) continue;
+    memcpy(w.words, pinned_ + (size_t)i * W_WORDS, sizeof(w.words));
+    if (&w == first_persistent) {
+      shared_err = w.words[W_ERR] & (ERR_TIMEOUT | ERR_CAPACITY);
+      shared_round_local = w.words[W_MAXROUND_LOCAL];
+    }
+    if (w.mseg >= 0 && w.pl.exec != SKY_EXEC_PLAIN) {
+      shared_err |= w.words[W_ERR] & (ERR_TIMEOUT | ERR_CAPACITY);
+      shared_round_merge = std::max(shared_round_merge, w.words[W_MAXROUND_MERGE]);
+    }
+  }
+  sky_status first_bad = SKY_OK;
+  std::string first_msg;
+  for (u32 i = 0; i < nq; ++i) {
+    Work& w = ws[i];
+    Query& q = *w.q;
+    if (q.n == 0) continue;
+    u32 e = w.words[W_ERR];
+    if (w.pl.exec != SKY_EXEC_PLAIN) e |= shared_err;
+    sky_status qs = SKY_OK;
+    std::string msg;
+    if (e & ERR_NAN) {
+      qs = SKY_EINVAL;
+      msg = "input contains NaN";
+    } else if (e & ERR_TIMEOUT) {
+      qs = SKY_ETIMEOUT;
+      msg = "a device-side wait timed out";
+    } else if (e & ERR_CAPACITY) {
+      qs = SKY_ENOMEM;
+      msg = "device-side capacity exceeded";
+    }
+    q.status = qs;
+    if (qs != SKY_OK) {
+      if (first_bad == SKY_OK) {
+        first_bad = qs;
+        first_msg = nq > 1 ? "query " + std::to_string(i) + ": " + msg : msg;
+      }
+      continue;
+    }
+    const u64 cnt = w.words[W_SKY];
+    Bufs& b = w.b;
+    const u64 n = w.pl.n;
+    if (!w.out_dev && cnt) CK(cudaMemcpyAsync(q.out_idx, b.out_dev, cnt * sizeof(u32), cudaMemcpyDeviceToHost, st));
+    // host-side diagnostics
+    if (q.out_stage && !is_device_ptr(q.out_stage)) {
+      CK(launch_output(b.stage_s, b.orig, b.spid, n, b.mask, reinterpret_cast<u8*>(b.keys[0]), b.vals[0], st));
+      CK(cudaMemcpyAsync(q.out_stage, b.keys[0], n, cudaMemcpyDeviceToHost, st));
+      if (q.out_pid && !is_device_ptr(q.out_pid))
+        CK(cudaMemcpyAsync(q.out_pid, b.vals[0], n * 4, cudaMemcpyDeviceToHost, st));
+    } else if (q.out_pid && !is_device_ptr(q.out_pid)) {
+      CK(launch_output(b.stage_s, b.orig, b.spid, n, b.mask, nullptr, b.vals[0], st));
+      CK(cudaMemcpyAsync(q.out_pid, b.vals[0], n * 4, cudaMemcpyDeviceToHost, st));
+    }
+    *q.out_count = cnt;
+    sky_stats& S = q.stats;
+    const bool shared = w.pl.exec != SKY_EXEC_PLAIN;
+    S.rounds_local = shared ? shared_round_local : w.words[W_MAXROUND_LOCAL];
+    S.rounds_merge = (shared && w.mseg >= 0) ? shared_round_merge : w.words[W_MAXROUND_MERGE];
+    S.reps_kept = w.pl.rep ? w.words[W_KEPT] : 0;
+    S.grid_dropped = w.words[W_HIST + ST_GRID];
+    S.rep_dropped = w.words[W_HIST + ST_REP];
+    S.local_union = (u64)w.words[W_HIST + ST_MERGE] + w.words[W_HIST + ST_SKY];
+    S.skyline = cnt;
+  }
+  record(7);
+  CK(cudaStreamSynchronize(st));
+  // batch statistics: sums over the queries, maxima of the round counts
+  for (u32 i = 0; i < nq; ++i) {
+    const sky_stats& S = queries[i].stats;
+    stats.n += S.n;
+    stats.d = std::max(stats.d, S.d);
+    stats.partitions += S.partitions;
+    stats.rounds_local = std::max(stats.rounds_local, S.rounds_local);
+    stats.rounds_merge = std::max(stats.rounds_merge, S.rounds_merge);
+    stats.reps_kept += S.reps_kept;
+    stats.grid_dropped += S.grid_dropped;
+    stats.rep_dropped += S.rep_dropped;
+    stats.local_union += S.local_union;
+    stats.skyline += S.skyline;
+  }
+  stats.launches = launch_counter() - launches0;
+  if (timing) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ev_[0], ev_[7]);
+    stats.ms_total = ms;
+    for (int i = 0; i < 6; ++i) {
+      float t = 0;
+      cudaEventElapsedTime(&t, ev_[i + 1], ev_[i + 2]);
+      stats.ms_phase[i] = t;
+    }
+    float tl = 0, tm = 0;
+    cudaEventElapsedTime(&tl, ev_[8], ev_[9]);
+    cudaEventElapsedTime(&tm, ev_[10], ev_[11]);
+    stats.ms_dom_local = tl;
+    stats.ms_dom_merge = tm;
+  }
+  if (first_bad != SKY_OK) return fail(first_bad, first_msg);
+  return SKY_OK;
+}
+
+}  // namespace sky

@@ -1,0 +1,84 @@
+// Host-side orchestration of Algorithm 2 over a batch of independent
+// skyline queries (internal; the C ABI is in sky_api.cu).
+#pragma once
+#include <mutex>
+#include <string>
+#include <vector>
+#include "../../include/skyline.h"
+#include "sky_internal.cuh"
+
+namespace sky {
+
+// Orders the persistent engine launches of several Runners that share a
+// device: each launch waits (on the GPU) for the one enqueued before it, so
+// two cooperative grids never compete for the SMs, while the other stages
+// of the Runners' batches still overlap.
+struct EngineGate {
+  std::mutex mu;
+  cudaEvent_t last = nullptr;  // completion event of the latest gated launch
+};
+
+// Checks one query's arguments (Section 3 parameters included); msg
+// receives the reason of a failure.
+sky_status validate_query(const float* points, u64 n, u32 d, const sky_params* params, std::string* msg);
+
+// Execution state that the pipeline needs: a device, a stream, a grow-only
+// device workspace, pinned host staging and timing events.  One Runner runs
+// one batch at a time.
+class Runner {
+ public:
+  int device = 0;
+  size_t budget = 0;            // workspace limit in bytes (0 = none)
+  cudaStream_t stream = nullptr;
+  int timing = 0;
+  std::string last_error;
+  sky_stats stats{};
+  EngineGate* gate = nullptr;   // set when several Runners share the device
+
+  ~Runner();
+  sky_status init(int dev, size_t mem_budget);
+  // Frees the device workspace (kept otherwise between batches).
+  void release();
+  size_t workspace_bytes() const { return ws_size_; }
+
+  // One query of a batch.  Inputs are caller-owned; out_idx has capacity
+  // >= n; out_pid / out_stage may be NULL.  Host or device pointers.
+  struct Query {
+    const float* points = nullptr;
+    u64 n = 0;
+    u32 d = 0;
+    const sky_params* params = nullptr;
+    u32* out_idx = nullptr;
+    u64* out_count = nullptr;
+    u32* out_pid = nullptr;
+    u8* out_stage = nullptr;
+    sky_status status = SKY_OK;   // out
+    sky_stats stats{};            // out: per-query statistics (no timing)
+  };
+
+  // Validates every query, then runs all of them: prep and sort per query,
+  // every local skyline of the batch in one persistent engine launch, every
+  // sequential final phase in a second one, outputs per query.  Blocks until
+  // the results are in the output buffers.  Returns the first failing
+  // status (queries[i].status says which).
+  sky_status run(Query* queries, u32 nq);
+
+  // Workspace bytes a query of this shape needs (for admission control).
+  static size_t query_bytes(u64 n, u32 d, const sky_params* params);
+
+ private:
+  char* ws_ = nullptr;
+  size_t ws_size_ = 0;
+  u32* pinned_ = nullptr;
+  size_t pinned_words_ = 0;
+  cudaEvent_t ev_[12] = {};
+  cudaEvent_t gate_ev_ = nullptr;
+  sky_status ensure_ws(size_t bytes);
+  sky_status ensure_pinned(size_t words);
+  sky_status fail(sky_status s, const std::string& msg);
+  void record(int i);
+};
+
+bool is_device_ptr(const void* p);
+
+}  // namespace sky

@@ -379,12 +379,13 @@ __global__ void k_useg(const u32* __restrict__ seg_off, u32 P, const u32* __rest
 
 // u in score order for the sequential final phase.
 template <int D>
-__global__ void k_gather_u(const u32* __restrict__ order, u64 n, const float* __restrict__ upts,
+__global__ void k_gather_u(const u32* __restrict__ order, u64 n, const u32* __restrict__ n_dev,
+                           const float* __restrict__ upts,
                            const uint4* __restrict__ uhc, const float* __restrict__ uscore,
                            const u32* __restrict__ upos, float* __restrict__ mpts, uint4* __restrict__ mhc,
                            float* __restrict__ mscore, u32* __restrict__ mpos) {
   u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
+  if (r >= n || (n_dev && r >= *n_dev)) return;
   u32 j = order[r];
   constexpr int V = vec_of(D);
   const float4* src = reinterpret_cast<const float4*>(upts) + (u64)j * V;
@@ -397,8 +398,10 @@ __global__ void k_gather_u(const u32* __restrict__ order, u64 n, const float* __
 }
 
 __global__ void k_scatter_alive(const u8* __restrict__ malive, const u32* __restrict__ mpos, u64 n,
-                                u8* __restrict__ alive, u8* __restrict__ stage_s, u8 code) {
+                                const u32* __restrict__ n_dev, u8* __restrict__ alive, u8* __restrict__ stage_s,
+                                u8 code) {
   u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n_dev && r >= *n_dev) return;
   if (r >= n || malive[r]) return;
   u32 p = mpos[r];
   alive[p] = 0;
@@ -542,22 +545,22 @@ cudaError_t launch_useg(const u32* seg_off, u32 P, const u32* excl, u64 n, const
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_u(const u32* order, u64 n, int d, const float* upts, const uint4* uhc,
+cudaError_t launch_gather_u(const u32* order, u64 n, const u32* n_dev, int d, const float* upts, const uint4* uhc,
                             const float* uscore, const u32* upos, float* mpts, uint4* mhc, float* mscore,
                             u32* mpos, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   return dispatch_d(d, [&](auto D) {
     note_launch();
-    k_gather_u<decltype(D)::value><<<grid_for(n), PT, 0, st>>>(order, n, upts, uhc, uscore, upos, mpts, mhc,
+    k_gather_u<decltype(D)::value><<<grid_for(n), PT, 0, st>>>(order, n, n_dev, upts, uhc, uscore, upos, mpts, mhc,
                                                               mscore, mpos);
   });
 }
 
-cudaError_t launch_scatter_alive(const u8* malive, const u32* mpos, u64 n, u8* alive, u8* stage_s,
-                                 u8 code, cudaStream_t st) {
+cudaError_t launch_scatter_alive(const u8* malive, const u32* mpos, u64 n, const u32* n_dev, u8* alive,
+                                 u8* stage_s, u8 code, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   note_launch();
-  k_scatter_alive<<<grid_for(n), PT, 0, st>>>(malive, mpos, n, alive, stage_s, code);
+  k_scatter_alive<<<grid_for(n), PT, 0, st>>>(malive, mpos, n, n_dev, alive, stage_s, code);
   return cudaGetLastError();
 }
 

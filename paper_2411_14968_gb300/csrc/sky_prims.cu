@@ -140,10 +140,19 @@ constexpr int RT = 256;       // threads per block == radix buckets
 constexpr int RIPT = 16;      // keys per thread
 constexpr u64 RTILE = (u64)RT * RIPT;
 
-__global__ void k_radix_hist(const u64* __restrict__ k, u64 n, int shift, u32 mask,
+// n_dev (optional): the element count lives in device memory and may be
+// below the capacity n the grid was sized for; blocks past it count nothing.
+__device__ __forceinline__ u64 radix_count(u64 n, const u32* n_dev) {
+  if (!n_dev) return n;
+  u64 m = *n_dev;
+  return m < n ? m : n;
+}
+
+__global__ void k_radix_hist(const u64* __restrict__ k, u64 n, const u32* __restrict__ n_dev, int shift, u32 mask,
                              u32* __restrict__ hist, u32 nb) {
   __shared__ u32 h[RT];
   const int tid = threadIdx.x, lane = tid & 31;
+  n = radix_count(n, n_dev);
   h[tid] = 0;
   __syncthreads();
   u64 base = (u64)blockIdx.x * RTILE;
@@ -160,11 +169,14 @@ __global__ void k_radix_hist(const u64* __restrict__ k, u64 n, int shift, u32 ma
 
 // Stable scatter: elements keep their input order inside each digit.
 __global__ void k_radix_scatter(const u64* __restrict__ kin, const u32* __restrict__ vin,
-                                u64* __restrict__ kout, u32* __restrict__ vout, u64 n, int shift,
-                                u32 mask, const u32* __restrict__ offs, u32 nb) {
+                                u64* __restrict__ kout, u32* __restrict__ vout, u64 n,
+                                const u32* __restrict__ n_dev, int shift, u32 mask,
+                                const u32* __restrict__ offs, u32 nb) {
   __shared__ u32 s_base[RT];
   __shared__ u32 s_w[RT / 32][RT];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  n = radix_count(n, n_dev);
+  if ((u64)blockIdx.x * RTILE >= n) return;
   s_base[tid] = offs[(u64)tid * nb + blockIdx.x];
 #pragma unroll
   for (int w = 0; w < RT / 32; ++w) s_w[w][tid] = 0;
@@ -221,7 +233,7 @@ cudaError_t scan_u8(const u8* in, u32* out, u64 n, bool exclusive, u32* tmp, cud
 size_t radix_hist_words(u64 n) { return (size_t)RT * (size_t)((n + RTILE - 1) / RTILE) + 1; }
 
 cudaError_t radix_sort(u64* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32* hist, u32* tmp,
-                       cudaStream_t st, int* out_sel) {
+                       cudaStream_t st, int* out_sel, const u32* n_dev) {
   int sel = 0;
   u64 nb = (n + RTILE - 1) / RTILE;
   if (n <= 1 || hi_bit <= lo_bit) {
@@ -232,11 +244,11 @@ cudaError_t radix_sort(u64* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32*
     int bits = hi_bit - shift < 8 ? hi_bit - shift : 8;
     u32 mask = (1u << bits) - 1u;
     note_launch();
-    k_radix_hist<<<(unsigned)nb, RT, 0, st>>>(k[sel], n, shift, mask, hist, (u32)nb);
+    k_radix_hist<<<(unsigned)nb, RT, 0, st>>>(k[sel], n, n_dev, shift, mask, hist, (u32)nb);
     cudaError_t e = scan_u32(hist, hist, (u64)RT * nb, true, false, tmp, st);
     if (e != cudaSuccess) return e;
     note_launch();
-    k_radix_scatter<<<(unsigned)nb, RT, 0, st>>>(k[sel], v[sel], k[sel ^ 1], v[sel ^ 1], n, shift,
+    k_radix_scatter<<<(unsigned)nb, RT, 0, st>>>(k[sel], v[sel], k[sel ^ 1], v[sel ^ 1], n, n_dev, shift,
                                                   mask, hist, (u32)nb);
     sel ^= 1;
   }

@@ -45,6 +45,36 @@ class SkyParams(ctypes.Structure):
     ]
 
 
+class SkyQuery(ctypes.Structure):
+    _fields_ = [
+        ("points", ctypes.c_void_p),
+        ("n", ctypes.c_uint64),
+        ("d", ctypes.c_uint32),
+        ("params", ctypes.POINTER(SkyParams)),
+        ("out_idx", ctypes.c_void_p),
+        ("out_count", ctypes.POINTER(ctypes.c_uint64)),
+        ("status", ctypes.c_int),
+    ]
+
+
+class SkyServeConfig(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("workers", ctypes.c_uint32),
+        ("max_batch", ctypes.c_uint32),
+        ("mem_budget_bytes", ctypes.c_uint64),
+    ]
+
+
+class SkyTicketInfo(ctypes.Structure):
+    _fields_ = [
+        ("queue_us", ctypes.c_double),
+        ("run_us", ctypes.c_double),
+        ("latency_us", ctypes.c_double),
+        ("batch_queries", ctypes.c_uint32),
+    ]
+
+
 class SkyStats(ctypes.Structure):
     _fields_ = [
         ("n", ctypes.c_uint64),
@@ -73,7 +103,8 @@ class SkyStats(ctypes.Structure):
 
 EXPORTS = ["sky_params_init", "sky_create", "sky_set_stream", "sky_set_timing", "sky_skyline",
            "sky_skyline_ex", "sky_get_stats", "sky_status_str", "sky_last_error", "sky_destroy",
-           "sky_probe_compare_rate", "sky_skyline_static"]
+           "sky_probe_compare_rate", "sky_skyline_static", "sky_skyline_batch", "sky_serve_config_init", "sky_query_bytes",
+           "sky_serve_start", "sky_submit", "sky_poll", "sky_wait", "sky_serve_stop"]
 
 _lock = threading.Lock()
 _lib = None
@@ -122,6 +153,22 @@ def load(build_if_missing: bool = True):
         L.sky_destroy.restype = None
         L.sky_probe_compare_rate.argtypes = [P, u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32)]
         L.sky_probe_compare_rate.restype = i32
+        L.sky_skyline_batch.argtypes = [P, ctypes.POINTER(SkyQuery), u32]
+        L.sky_skyline_batch.restype = i32
+        L.sky_serve_config_init.argtypes = [ctypes.POINTER(SkyServeConfig)]
+        L.sky_serve_config_init.restype = None
+        L.sky_query_bytes.argtypes = [u64, u32, ctypes.POINTER(SkyParams)]
+        L.sky_query_bytes.restype = u64
+        L.sky_serve_start.argtypes = [P, ctypes.POINTER(SkyServeConfig)]
+        L.sky_serve_start.restype = i32
+        L.sky_submit.argtypes = [P, P, u64, u32, ctypes.POINTER(SkyParams), ctypes.POINTER(u64)]
+        L.sky_submit.restype = i32
+        L.sky_poll.argtypes = [P, u64]
+        L.sky_poll.restype = i32
+        L.sky_wait.argtypes = [P, u64, P, ctypes.POINTER(u64), ctypes.c_int64, ctypes.POINTER(SkyTicketInfo)]
+        L.sky_wait.restype = i32
+        L.sky_serve_stop.argtypes = [P]
+        L.sky_serve_stop.restype = i32
         L.sky_skyline_static.argtypes = [P, u64, u32, P, ctypes.POINTER(u64), P]
         L.sky_skyline_static.restype = i32
         _lib = L
@@ -258,6 +305,109 @@ class Context:
             return res[: cnt.value], pid[:n], stage[:n]
         return res[: cnt.value]
 
+    # ---- serving (continuous batching) --------------------------------
+    def serve_start(self, workers: int = 2, max_batch: int = 64, mem_budget_bytes: int = 0):
+        cfg = SkyServeConfig()
+        self._L.sky_serve_config_init(ctypes.byref(cfg))
+        cfg.workers, cfg.max_batch, cfg.mem_budget_bytes = int(workers), int(max_batch), int(mem_budget_bytes)
+        st = self._L.sky_serve_start(self._h, ctypes.byref(cfg))
+        if st != SKY_OK:
+            raise SkylineError(st, self._L.sky_status_str(st).decode())
+
+    def submit(self, points, params: SkyParams | None = None) -> int:
+        """Queues Sky(points); returns the ticket.  points (host numpy or
+        CUDA torch float32 [N, d]) is kept alive by the binding until wait()."""
+        if params is None:
+            params = make_params()
+        if _is_cuda_tensor(points):
+            points = points.contiguous()
+            ptr = points.data_ptr()
+        else:
+            points = np.ascontiguousarray(points, dtype=np.float32)
+            ptr = points.ctypes.data
+        n, d = points.shape
+        t = ctypes.c_uint64(0)
+        st = self._L.sky_submit(self._h, ctypes.c_void_p(ptr), n, d, ctypes.byref(params), ctypes.byref(t))
+        if st != SKY_OK:
+            raise SkylineError(st, self._L.sky_status_str(st).decode())
+        if not hasattr(self, "_inflight"):
+            self._inflight = {}
+        self._inflight[t.value] = (points, params, n)
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        st = self._L.sky_poll(self._h, int(ticket))
+        if st == SKY_OK:
+            return True
+        if st == SKY_EBUSY:
+            return False
+        raise SkylineError(st, self._L.sky_status_str(st).decode())
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        """Result of a ticket: (numpy uint32 ascending indices, info dict with
+        queue_us / run_us / latency_us / batch_queries)."""
+        _, _, n = self._inflight[ticket]
+        out = np.zeros(max(n, 1), dtype=np.uint32)
+        cnt = ctypes.c_uint64(0)
+        info = SkyTicketInfo()
+        st = self._L.sky_wait(self._h, int(ticket), out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt),
+                              int(timeout_us), ctypes.byref(info))
+        if st == SKY_EBUSY:
+            raise TimeoutError(f"ticket {ticket} still in flight")
+        self._inflight.pop(ticket, None)
+        if st != SKY_OK:
+            raise SkylineError(st, self._L.sky_status_str(st).decode())
+        return out[: cnt.value], {f: getattr(info, f) for f, _ in SkyTicketInfo._fields_}
+
+    def serve_stop(self):
+        self._check(self._L.sky_serve_stop(self._h))
+
+    def skyline_batch(self, queries):
+        """Several independent queries in one batch (sky_skyline_batch).
+
+        queries: a list of (points, params) pairs, points a host numpy or
+        CUDA torch float32 [N, d] array, params a SkyParams or None.  Returns
+        the list of index arrays (numpy for host input, CUDA torch int32 for
+        device input)."""
+        nq = len(queries)
+        arr = (SkyQuery * max(nq, 1))()
+        keep, outs, counts = [], [], []
+        stream_set = False
+        for i, (pts, params) in enumerate(queries):
+            if params is None:
+                params = make_params()
+            cnt = ctypes.c_uint64(0)
+            if _is_cuda_tensor(pts):
+                import torch
+                pts = pts.contiguous()
+                n, d = pts.shape
+                if not stream_set:
+                    self.set_stream(torch.cuda.current_stream(pts.device).cuda_stream)
+                    stream_set = True
+                out = torch.empty(max(n, 1), dtype=torch.int32, device=pts.device)
+                arr[i].points, arr[i].out_idx = pts.data_ptr(), out.data_ptr()
+            else:
+                pts = np.ascontiguousarray(pts, dtype=np.float32)
+                n, d = pts.shape
+                out = np.zeros(max(n, 1), dtype=np.uint32)
+                arr[i].points = pts.ctypes.data
+                arr[i].out_idx = out.ctypes.data
+            arr[i].n, arr[i].d = n, d
+            arr[i].params = ctypes.pointer(params)
+            arr[i].out_count = ctypes.pointer(cnt)
+            keep.append((pts, params))
+            outs.append(out)
+            counts.append(cnt)
+        if not stream_set:
+            self.set_stream(0)
+        self._check(self._L.sky_skyline_batch(self._h, arr, nq))
+        return [o[: c.value] for o, c in zip(outs, counts)]
+
+
+def query_bytes(n: int, d: int, params: SkyParams | None = None) -> int:
+    """Device memory one query of this shape takes in a batch (bytes)."""
+    return int(load().sky_query_bytes(int(n), int(d), ctypes.byref(params) if params is not None else None))
+
 
 STATIC_MAX_POINTS = 65536
 
@@ -285,7 +435,6 @@ def skyline_static(points, out=None):
     if st != SKY_OK:
         raise SkylineError(st, L.sky_status_str(st).decode())
     return out[: cnt.value]
-
 
 _default_ctx = None
 
