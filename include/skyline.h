@@ -169,6 +169,19 @@ typedef struct {
    the batch's (sums over queries; maxima of round counts). */
 sky_status sky_skyline_batch(sky_ctx* ctx, sky_query* queries, uint32_t nq);
 
+/* Autotuner of the dominance engine's knobs (chunk_min, chunk_max,
+   chunk_alpha_x4, dom_block of sky_params): the SFS chunk sizes of the
+   engine's rounds and the dominator block a CTA stages in shared memory.
+   They decide how Algorithm 1 is cut into parallel work, never the result.
+   Runs the query (points, n, d with the method parameters in *params) up
+   to max_trials times (0 = 48) with candidate knobs, timing each run with
+   CUDA events on the context's stream (coordinate descent from the
+   defaults, two sweeps), and writes the fastest knobs into *params;
+   *best_ms receives its time.  Blocks; allocates one N-index device buffer
+   for the trial outputs. */
+sky_status sky_autotune(sky_ctx* ctx, const float* points, uint64_t n, uint32_t d, sky_params* params,
+                        uint32_t max_trials, double* best_ms);
+
 /* ---- serving: a request loop with continuous batching ----------------
    sky_submit queues a query and returns at once.  Worker threads of the
    context take queued queries in arrival order into batches whose device

@@ -34,6 +34,10 @@ struct sky_ctx {
   std::string serve_error;
 };
 
+namespace sky {
+int ctx_timing(sky_ctx* ctx) { return ctx ? ctx->run.timing : 0; }
+}  // namespace sky
+
 namespace {
 
 sky_status run_one(sky_ctx* ctx, const float* points, u64 n, u32 d, const sky_params* pa, u32* out_idx,

@@ -56,7 +56,8 @@ constexpr u32 A_BLOCKS = 1;             // window blocks of phase A
 constexpr u32 MAX_SEG = 4096;           // segments per launch (shared-memory prefix)
 constexpr u64 WAIT_NS = 4000000000ull;  // bound of every wait
 
-enum { C_A0 = 0, C_A1 = 1, C_B0 = 2, C_B1 = 3, C_BAR_COUNT = 4, C_BAR_GEN = 5, C_ABORT = 6, C_MAXROUND = 7 };
+enum { C_A0 = 0, C_A1 = 1, C_B0 = 2, C_B1 = 3, C_BAR_COUNT = 4, C_BAR_GEN = 5, C_ABORT = 6, C_MAXROUND = 7,
+       C_PROGRESS = 8 };
 
 __device__ __forceinline__ u64 globaltimer() {
   u64 t;
@@ -113,7 +114,10 @@ __device__ bool mbar_wait(u64* bar, u32 parity, u32* err, u32* ctl) {
 // Generic-proxy writes of global memory made visible to later bulk copies.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
-// Grid-wide barrier of the cooperative launch (bounded wait).
+// Grid-wide barrier of the cooperative launch.  The wait is bounded by
+// progress, not by its length: a CTA gives up (ERR_TIMEOUT, abort) only
+// after WAIT_NS in which no work item anywhere completed, so a long round
+// of a large input is not mistaken for a hang.
 __device__ bool grid_barrier(u32* ctl, u32* err) {
   __shared__ int s_ok;
   __syncthreads();
@@ -129,8 +133,14 @@ __device__ bool grid_barrier(u32* ctl, u32* err) {
       atomicAdd(ctl + C_BAR_GEN, 1u);
     } else {
       u64 t0 = globaltimer();
+      u32 seen = ld_vol_u32(ctl + C_PROGRESS);
       while (ld_vol_u32(ctl + C_BAR_GEN) == gen) {
         if (ld_vol_u32(ctl + C_ABORT)) { ok = false; break; }
+        const u32 now = ld_vol_u32(ctl + C_PROGRESS);
+        if (now != seen) {
+          seen = now;
+          t0 = globaltimer();
+        }
         if (globaltimer() - t0 > WAIT_NS) {
           atomicOr(err, ERR_TIMEOUT);
           atomicExch(ctl + C_ABORT, 1u);
@@ -662,6 +672,7 @@ __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
           case 7: run_item<7>(phase, P, sd, cur, nxt, s, l, tiles_s, s_tiles[s], round, S); break;
           default: run_item<8>(phase, P, sd, cur, nxt, s, l, tiles_s, s_tiles[s], round, S); break;
         }
+        if (threadIdx.x == 0) atomicAdd(P.ctl + C_PROGRESS, 1u);
         if (ld_vol_u32(P.ctl + C_ABORT)) break;
       }
       if (!grid_barrier(P.ctl, P.err)) return;

@@ -116,6 +116,11 @@ void Server::shutdown() {
   I.cv_work.notify_all();
   for (auto& t : I.workers) t.join();
   I.workers.clear();
+  // the gate refers to an event of one of the Runners destroyed below
+  {
+    std::lock_guard<std::mutex> g(I.gate.mu);
+    I.gate.last = nullptr;
+  }
   I.runners.clear();
   for (auto s : I.streams) {
     cudaSetDevice(I.device);

@@ -1,0 +1,102 @@
+// sky_autotune: picks the dominance engine's tuning knobs for a workload by
+// measurement.  The knobs change only how Algorithm 1 is cut into parallel
+// work (chunk sizes of the SFS rounds, the dominator block a CTA stages in
+// shared memory), never the result, so any choice is exact; the tuner
+// times whole queries (CUDA events around the call on the context's stream)
+// and keeps the fastest.
+//
+// Search: coordinate descent from the built-in defaults.  For each knob in
+// turn every candidate value is tried with the others held at their best
+// values so far; two sweeps, within a trial budget.  Each candidate runs
+// twice and counts its faster run (the first may pay for growing the
+// workspace).
+#include <cfloat>
+#include <cstring>
+#include <vector>
+#include "../../include/skyline.h"
+#include "sky_internal.cuh"
+
+namespace sky {
+int ctx_timing(sky_ctx* ctx);
+}
+
+namespace {
+
+struct Knob {
+  uint32_t sky_params::*field;
+  std::vector<uint32_t> values;
+};
+
+}  // namespace
+
+extern "C" sky_status sky_autotune(sky_ctx* ctx, const float* points, uint64_t n, uint32_t d, sky_params* params,
+                                   uint32_t max_trials, double* best_ms) {
+  if (!ctx || !params || !best_ms || params->struct_size != sizeof(sky_params)) return SKY_EINVAL;
+  if (n == 0) {
+    *best_ms = 0;
+    return SKY_OK;
+  }
+  if (max_trials == 0) max_trials = 48;
+  uint32_t* out = nullptr;
+  if (cudaMalloc(&out, n * sizeof(uint32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    return SKY_ENOMEM;
+  }
+  const int timing_was = sky::ctx_timing(ctx);
+  sky_set_timing(ctx, 1);
+  sky_params cur = *params;
+  if (!cur.dom_block) cur.dom_block = 1024;
+  if (!cur.chunk_min) cur.chunk_min = 4096;
+  if (!cur.chunk_max) cur.chunk_max = 65536;
+  if (!cur.chunk_alpha_x4) cur.chunk_alpha_x4 = 8;
+  const Knob knobs[] = {
+      {&sky_params::dom_block, {256, 512, 1024, 2048}},
+      {&sky_params::chunk_max, {8192, 16384, 32768, 65536, 131072, 262144}},
+      {&sky_params::chunk_alpha_x4, {2, 4, 8, 16}},
+      {&sky_params::chunk_min, {1024, 4096, 16384}},
+  };
+  uint32_t trials = 0;
+  sky_status status = SKY_OK;
+  auto measure = [&](const sky_params& p, double* ms) -> sky_status {
+    double best = DBL_MAX;
+    for (int rep = 0; rep < 2; ++rep) {
+      uint64_t cnt = 0;
+      sky_status s = sky_skyline(ctx, points, n, d, &p, out, &cnt);
+      if (s != SKY_OK) return s;
+      sky_stats st;
+      sky_get_stats(ctx, &st);
+      if (st.ms_total < best) best = st.ms_total;
+    }
+    *ms = best;
+    ++trials;
+    return SKY_OK;
+  };
+  double cur_ms = 0;
+  status = measure(cur, &cur_ms);
+  for (int sweep = 0; sweep < 2 && status == SKY_OK; ++sweep) {
+    bool changed = false;
+    for (const Knob& k : knobs) {
+      for (uint32_t v : k.values) {
+        if (trials >= max_trials || status != SKY_OK) break;
+        if (cur.*(k.field) == v) continue;
+        sky_params cand = cur;
+        cand.*(k.field) = v;
+        if (cand.chunk_max < cand.chunk_min) continue;
+        double ms = 0;
+        status = measure(cand, &ms);
+        if (status == SKY_OK && ms < cur_ms) {
+          cur = cand;
+          cur_ms = ms;
+          changed = true;
+        }
+      }
+    }
+    if (!changed) break;
+  }
+  cudaFree(out);
+  sky_set_timing(ctx, timing_was);
+  if (status != SKY_OK) return status;
+  *params = cur;
+  *best_ms = cur_ms;
+  return SKY_OK;
+}

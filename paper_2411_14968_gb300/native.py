@@ -104,7 +104,7 @@ class SkyStats(ctypes.Structure):
 EXPORTS = ["sky_params_init", "sky_create", "sky_set_stream", "sky_set_timing", "sky_skyline",
            "sky_skyline_ex", "sky_get_stats", "sky_status_str", "sky_last_error", "sky_destroy",
            "sky_probe_compare_rate", "sky_skyline_static", "sky_skyline_batch", "sky_serve_config_init", "sky_query_bytes",
-           "sky_serve_start", "sky_submit", "sky_poll", "sky_wait", "sky_serve_stop"]
+           "sky_serve_start", "sky_submit", "sky_poll", "sky_wait", "sky_serve_stop", "sky_autotune"]
 
 _lock = threading.Lock()
 _lib = None
@@ -159,6 +159,8 @@ def load(build_if_missing: bool = True):
         L.sky_serve_config_init.restype = None
         L.sky_query_bytes.argtypes = [u64, u32, ctypes.POINTER(SkyParams)]
         L.sky_query_bytes.restype = u64
+        L.sky_autotune.argtypes = [P, P, u64, u32, ctypes.POINTER(SkyParams), u32, ctypes.POINTER(ctypes.c_double)]
+        L.sky_autotune.restype = i32
         L.sky_serve_start.argtypes = [P, ctypes.POINTER(SkyServeConfig)]
         L.sky_serve_start.restype = i32
         L.sky_submit.argtypes = [P, P, u64, u32, ctypes.POINTER(SkyParams), ctypes.POINTER(u64)]
@@ -304,6 +306,31 @@ class Context:
         if with_diag:
             return res[: cnt.value], pid[:n], stage[:n]
         return res[: cnt.value]
+
+    def autotune(self, points, params: SkyParams | None = None, max_trials: int = 0, **kw):
+        """Tunes the engine knobs for this workload (sky_autotune); returns
+        (tuned SkyParams, best time in ms).  points: host numpy or CUDA
+        torch float32 [N, d]."""
+        if params is None:
+            params = make_params(**kw)
+        else:
+            sp = SkyParams()
+            ctypes.memmove(ctypes.byref(sp), ctypes.byref(params), ctypes.sizeof(SkyParams))
+            params = sp
+        if _is_cuda_tensor(points):
+            import torch
+            points = points.contiguous()
+            ptr = points.data_ptr()
+            self.set_stream(torch.cuda.current_stream(points.device).cuda_stream)
+        else:
+            points = np.ascontiguousarray(points, dtype=np.float32)
+            ptr = points.ctypes.data
+            self.set_stream(0)
+        n, d = points.shape
+        ms = ctypes.c_double(0)
+        self._check(self._L.sky_autotune(self._h, ctypes.c_void_p(ptr), n, d, ctypes.byref(params),
+                                         int(max_trials), ctypes.byref(ms)))
+        return params, ms.value
 
     # ---- serving (continuous batching) --------------------------------
     def serve_start(self, workers: int = 2, max_batch: int = 64, mem_budget_bytes: int = 0):

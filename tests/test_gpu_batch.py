@@ -80,3 +80,15 @@ def test_batch_rejects_invalid_query(ctx):
     with pytest.raises(native.SkylineError):
         ctx.skyline_batch([(good, None), (np.zeros((4, 9), np.float32), None)])
     assert ctx.skyline_batch([(good, None)])[0].shape[0] > 0
+
+
+def test_autotune_keeps_result_and_improves_or_keeps_time(ctx):
+    from paper_2411_14968_gb300 import native
+    x = datagen.anticorrelated(60000, 6, 51)
+    base = native.make_params(scheme="sliced", p=8, rep="sorted")
+    want = ctx.skyline(x, params=base)
+    tuned, ms = ctx.autotune(x, base, max_trials=12)
+    assert ms > 0
+    assert tuned.scheme == base.scheme and tuned.num_partitions == 8 and tuned.rep == base.rep
+    assert tuned.dom_block % 32 == 0 and tuned.chunk_max >= tuned.chunk_min > 0
+    np.testing.assert_array_equal(ctx.skyline(x, params=tuned), want)

@@ -1,0 +1,81 @@
+"""Full-size parity: the GPU skyline of each full-size workload, in the
+launch configuration the benchmark times (the queries of a workload batched
+into one call), must be the oracle's skyline exactly -- same count and same
+SHA-256 of the ascending index array.  The expected values were written by
+tests/golden/make_full_size.py, which calls only the oracle; the input's own
+hash is checked first so that a generator difference between machines is
+reported as such, not as a skyline mismatch."""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2411_14968_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLD = json.load(open(os.path.join(HERE, "golden", "full_size_skylines.json")))
+WORK = json.load(open(os.path.join(HERE, "golden", "workcounts_ant_1m_d6.json")))["variants"]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2411_14968_gb300 import native
+    c = native.Context(0)
+    yield c
+    c.close()
+
+
+def _data(name):
+    g = GOLD[name]
+    x = datagen.make(g["kind"], g["n"], g["d"], g["seed"])
+    assert hashlib.sha256(x.astype("<f4").tobytes()).hexdigest() == g["input_sha256"], \
+        f"{name}: the generator produced different input on this machine"
+    return x, g
+
+
+def _check_batch(ctx, name, variants):
+    import torch
+    from paper_2411_14968_gb300 import native
+    x, g = _data(name)
+    xt = torch.from_numpy(x).cuda()
+    params = [native.make_params(**kw) for kw in variants]
+    res = ctx.skyline_batch([(xt, p) for p in params])
+    torch.cuda.synchronize()
+    for kw, r in zip(variants, res):
+        idx = r.cpu().numpy().astype("<u4")
+        assert idx.shape[0] == g["skyline"], (name, kw)
+        assert hashlib.sha256(idx.tobytes()).hexdigest() == g["skyline_sha256"], (name, kw)
+    return xt
+
+
+def test_anticorrelated_1m_d6_bench_config(ctx):
+    from paper_2411_14968_gb300 import native
+    variants = [("sliced", dict(scheme="sliced", p=64)),
+                ("sliced_rep", dict(scheme="sliced", p=64, rep="sorted")),
+                ("angular", dict(scheme="angular", slices=[4, 2, 2, 2, 2])),
+                ("angular_rep", dict(scheme="angular", slices=[4, 2, 2, 2, 2], rep="sorted"))]
+    xt = _check_batch(ctx, "anticorrelated_1m_d6", [kw for _, kw in variants])
+    # |u| of every variant equals the oracle's (the local phase is exact too)
+    for name, kw in variants:
+        ctx.skyline(xt, params=native.make_params(**kw))
+        assert ctx.stats()["local_union"] == WORK[name]["local_union"], name
+
+
+@pytest.mark.parametrize("name", ["independent_q_4m_d8", "correlated_q_4m_d8"])
+def test_quantised_4m_d8_grid_vs_random(ctx, name):
+    _check_batch(ctx, name, [dict(scheme="grid", slices=[2] * 8), dict(scheme="random", p=256, seed=11),
+                             dict(scheme="grid", slices=[2] * 8, merge="noseq")])
+
+
+def test_skewed_angular_p128_reps(ctx):
+    sl = [4, 4, 2, 2, 2]
+    _check_batch(ctx, "skewed_200k_d6", [dict(scheme="angular", slices=sl, normalize=True, rep="sorted"),
+                                         dict(scheme="angular", slices=sl, normalize=True, rep="sorted",
+                                              merge="noseq")])

@@ -73,6 +73,22 @@ def test_results_same_alone_and_in_the_mix(native_mod):
     assert all(i["latency_us"] >= i["run_us"] >= 0 for i in infos)
 
 
+def test_restart_after_stop(native_mod):
+    # stop and start again, with two workers (whose engine launches are
+    # ordered by a gate that must not outlive the stopped workers)
+    native = native_mod
+    qs = [(datagen.anticorrelated(5000 + 3000 * i, 4 + i % 4, 80 + i), native.make_params(scheme="sliced", p=4))
+          for i in range(6)]
+    with native.Context(0) as ctx:
+        alone = [ctx.skyline(x, params=p) for x, p in qs]
+        for workers, mb in ((2, 4), (1, 1), (2, 64), (2, 2)):
+            ctx.serve_start(workers=workers, max_batch=mb)
+            ts = [ctx.submit(x, p) for x, p in qs]
+            for t, want in zip(ts, alone):
+                np.testing.assert_array_equal(ctx.wait(t)[0], want)
+            ctx.serve_stop()
+
+
 def test_admission_by_device_memory(native_mod):
     native = native_mod
     qs = [(datagen.anticorrelated(20000, 6, 70 + i), native.make_params(scheme="sliced", p=4)) for i in range(12)]
