@@ -283,8 +283,21 @@ def gpu_arm(args, rank, world, local):
     xt = torch.from_numpy(x).to(dev)
     ctx = native.Context(local)
     ctx.set_timing(True)
-    persistent = {name: native.make_params(exec="persistent", **kw) for name, kw in VARIANTS}
-    plain = {name: native.make_params(exec="plain", **kw) for name, kw in VARIANTS}
+    tuning = None
+    knobs = {}
+    if not args.no_autotune:
+        # the autotuner picks the engine knobs (SFS chunk sizes, dominator
+        # block) on the first variant; every variant and form then uses them
+        p0 = native.make_params(**VARIANTS[0][1])
+        default_ms = None
+        ctx.skyline(xt, params=p0)
+        ctx.skyline(xt, params=p0)
+        default_ms = ctx.stats()["ms_total"]
+        tuned, best_ms = ctx.autotune(xt, p0, max_trials=40)
+        knobs = {k: getattr(tuned, k) for k in ("chunk_min", "chunk_max", "chunk_alpha_x4", "dom_block")}
+        tuning = {"tuned_on": VARIANTS[0][0], "knobs": knobs, "default_knobs_ms": default_ms, "tuned_ms": best_ms}
+    persistent = {name: native.make_params(exec="persistent", **kw, **knobs) for name, kw in VARIANTS}
+    plain = {name: native.make_params(exec="plain", **kw, **knobs) for name, kw in VARIANTS}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     names = [name for name, _ in VARIANTS]
@@ -438,6 +451,7 @@ def gpu_arm(args, rank, world, local):
             "roofline": roof,
             "cpu_baseline": cpu,
             "serving": serving,
+            "autotune": tuning,
             "batched": batched_detail,
             "variants": per_variant,
         }
@@ -445,6 +459,21 @@ def gpu_arm(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def ncu_case():
+    """The small case the engine's ncu capture runs: its two k_engine launches
+    of the second call (local phase, merge) are the captured ones."""
+    import torch
+    from paper_2411_14968_gb300 import datagen, native
+    x = datagen.anticorrelated(200_000, 6, SEED)
+    xt = torch.from_numpy(x).cuda()
+    with native.Context(0) as ctx:
+        p = native.make_params(scheme="sliced", p=64)
+        for _ in range(2):
+            r = ctx.skyline(xt, params=p)
+        torch.cuda.synchronize()
+        print(f"ncu case: |Sky| = {r.shape[0]}, {ctx.stats()['launches']} launches per call")
 
 
 def main():
@@ -455,11 +484,18 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="run the small profiling case only: one query (anticorrelated N=200k, d=6, Sliced p=64) "
+                         "twice, default knobs, no timing")
     # FP32 compare peak: 152 SMs x 64 compare lanes per SM per clock x 2.07 GHz
     # (the compare-rate probe of the library measures 58.6 per SM per clock)
     ap.add_argument("--compare-peak-tcmp", type=float, default=SM_COUNT * 64 * 2.07e9 / 1e12)
     args = ap.parse_args()
     rank, world, local = dist_env()
+    if args.ncu_case:
+        ncu_case()
+        return
     if args.impl == "reference":
         reference_arm(args, rank, world)
         return

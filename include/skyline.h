@@ -83,10 +83,10 @@ typedef struct {
   sky_merge merge;             /* final phase (Section 4.2) */
   sky_exec exec;               /* launch form of the local-skyline phase */
   /* tuning knobs of the dominance engine; 0 selects the built-in default */
-  uint32_t chunk_min;          /* smallest SFS chunk of a partition (points) */
-  uint32_t chunk_max;          /* largest SFS chunk of a partition (points) */
-  uint32_t chunk_alpha_x4;     /* next chunk = alpha/4 x current window size, clamped */
-  uint32_t dom_block;          /* dominator block per work item (points, multiple of 32) */
+  uint32_t chunk_min;          /* smallest SFS chunk of a partition (points; default 1024) */
+  uint32_t chunk_max;          /* largest SFS chunk of a partition (points; default 262144) */
+  uint32_t chunk_alpha_x4;     /* next chunk = alpha/4 x current window size, clamped (default 16) */
+  uint32_t dom_block;          /* dominator block per work item (points, multiple of 32, <= 2048; default 1024) */
 } sky_params;
 
 /* Per-call statistics (the last sky_skyline call of the context). */

@@ -337,11 +337,22 @@ __device__ __forceinline__ u32 items_b(const SegState& s, u32 DB) {
   return dtiles_of(s) * (wbB + ceil_div(s.dlen, DB));
 }
 
+// One work item as the producer thread planned it.
+struct Meta {
+  u32 item;    // item index of the phase (>= total: no item)
+  u32 s;       // segment
+  u32 tile;    // candidate tile (phase A) or dense-list tile (phase B)
+  u32 tgid;    // global tile id (completion counters)
+  u32 cnt;     // dominators staged in the item's buffer
+  u32 base;    // index of the first staged dominator in its source
+  u32 dense;   // 1: the dominators are dense-list points (FP32 via dpos)
+  u32 copied;  // 1: a bulk copy into the item's buffer was issued
+};
+
 struct Shared {
-  uint4 codes[DBMAX];
-  u64 bar;
-  u32 bar_phase;
-  u32 item;
+  Meta meta[2];
+  u64 bar[2];
+  u32 bar_phase[2];
   u32 flag;
   u32 warp_tot[WARPS];
   u32 carry;
@@ -398,18 +409,54 @@ __device__ __forceinline__ u32 find_segment(const u32* pre, u32 nseg, u32 it) {
   return lo;
 }
 
-// Stages codes[lo, lo + cnt) into shared memory; returns false on timeout.
-__device__ bool stage_block(const uint4* codes, u32 cnt, Shared& S, const Params& P) {
-  if (cnt == 0) return true;
-  if (threadIdx.x == 0) {
-    fence_proxy_async();
-    mbar_expect_tx(&S.bar, cnt * 16u);
-    bulk_g2s(S.codes, codes, cnt * 16u, &S.bar);
+// Producer (thread 0 only): takes the next item of the phase and starts the
+// bulk copy of its dominator block's FP16 images into buffer `slot`.  The
+// buffer is free: every warp has passed the end of the item that used it.
+__device__ void produce(const Params& P, int phase, const SegState* cur, const u32* s_items, const u32* s_tiles,
+                        u32 total, u32* counter, uint4* buf, int slot, Shared& S) {
+  Meta m;
+  m.item = atomicAdd(counter, 1u);
+  m.copied = 0;
+  m.cnt = 0;
+  if (m.item < total) {
+    const u32 DB = P.cfg.dom_block;
+    m.s = find_segment(s_items, P.nseg, m.item);
+    const u32 l = m.item - s_items[m.s];
+    const u32 tiles_s = s_tiles[m.s + 1] - s_tiles[m.s];
+    m.tile = l % tiles_s;  // block-major numbering: item l = block * tiles + tile
+    const u32 b = l / tiles_s;
+    m.tgid = s_tiles[m.s] + m.tile;
+    const u32 wlen = ld_cg_u32(&cur[m.s].wlen);
+    const uint4* codes;
+    if (phase == 0) {
+      m.cnt = min(wlen, DB);
+      m.base = 0;
+      m.dense = 0;
+      codes = P.segs[m.s].whc;
+    } else {
+      const u32 dlen = ld_cg_u32(&cur[m.s].dlen);
+      const u32 wb = ceil_div(wlen, DB);
+      const u32 wbB = wb > A_BLOCKS ? wb - A_BLOCKS : 0;
+      if (b < wbB) {
+        m.base = (A_BLOCKS + b) * DB;
+        m.cnt = min(DB, wlen - m.base);
+        m.dense = 0;
+        codes = P.segs[m.s].whc + m.base;
+      } else {
+        m.base = (b - wbB) * DB;
+        m.cnt = min(DB, dlen - m.base);
+        m.dense = 1;
+        codes = P.segs[m.s].dhc + m.base;
+      }
+    }
+    if (m.cnt) {
+      fence_proxy_async();
+      mbar_expect_tx(&S.bar[slot], m.cnt * 16u);
+      bulk_g2s(buf, codes, m.cnt * 16u, &S.bar[slot]);
+      m.copied = 1;
+    }
   }
-  bool ok = mbar_wait(&S.bar, S.bar_phase, P.err, P.ctl);
-  __syncthreads();
-  if (threadIdx.x == 0) S.bar_phase ^= 1u;
-  return ok;
+  S.meta[slot] = m;
 }
 
 template <int D>
@@ -423,21 +470,21 @@ __device__ void load_cand(const SegDesc& sd, u32 pos, bool valid, Cands& c, int 
 
 // Phase A item: tile `tile` of the chunk against window block 0.
 template <int D>
-__device__ void item_a(const Params& P, const SegDesc& sd, SegState* cur, SegState* nxt, u32 s, u32 tile,
-                       u32 tgid, u32 round, Shared& S) {
+__device__ void item_a(const Params& P, const SegDesc& sd, SegState* cur, SegState* nxt, const Meta& mt,
+                       const uint4* staged, u32 round, Shared& S) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 DB = P.cfg.dom_block;
+  const u32 s = mt.s, tgid = mt.tgid;
   SegState cs;
   cs.cur = ld_cg_u32(&cur[s].cur);
   cs.cend = ld_cg_u32(&cur[s].cend);
   cs.wlen = ld_cg_u32(&cur[s].wlen);
   cs.tiles = ld_cg_u32(&cur[s].tiles);
-  const u32 cnt = min(cs.wlen, min(DB, DBMAX));
+  const u32 cnt = mt.cnt;
   const u32 per_tile = max(1u, min(ceil_div(cs.wlen, DB), A_BLOCKS));
-  const u32 gbase = cs.cur + tile * TILE + warp * GS;
+  const u32 gbase = cs.cur + mt.tile * TILE + warp * GS;
 
   if (cnt) {
-    if (!stage_block(sd.whc, cnt, S, P)) return;
     Cands c;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -446,7 +493,7 @@ __device__ void item_a(const Params& P, const SegDesc& sd, SegState* cur, SegSta
     }
     if (__any_sync(FULL, any_alive(c))) {
       DomSrc src{sd.win, nullptr, 0};
-      scan_smem<D>(S.codes, cnt, src, sd.pts, c);
+      scan_smem<D>(staged, cnt, src, sd.pts, c);
 #pragma unroll
       for (int r = 0; r < R; ++r)
         if (c.was[r] && !c.alive[r]) sd.alive[c.pos[r]] = 0;
@@ -504,11 +551,12 @@ __device__ void item_a(const Params& P, const SegDesc& sd, SegState* cur, SegSta
 // Phase B item: dense tile `dt` against window block A_BLOCKS + b, or dense
 // block b - (window blocks of phase B).
 template <int D>
-__device__ void item_b(const Params& P, const SegDesc& sd, SegState* cur, SegState* nxt, u32 s, u32 dt, u32 b,
-                       u32 tgid, u32 round, Shared& S) {
+__device__ void item_b(const Params& P, const SegDesc& sd, SegState* cur, SegState* nxt, const Meta& mt,
+                       const uint4* staged, u32 round, Shared& S) {
   constexpr int V = vec_of(D);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 DB = P.cfg.dom_block;
+  const u32 s = mt.s, tgid = mt.tgid;
   SegState cs;
   cs.cur = ld_cg_u32(&cur[s].cur);
   cs.cend = ld_cg_u32(&cur[s].cend);
@@ -519,23 +567,9 @@ __device__ void item_b(const Params& P, const SegDesc& sd, SegState* cur, SegSta
   const u32 wbB = wb > A_BLOCKS ? wb - A_BLOCKS : 0;
   const u32 dtiles = ceil_div(cs.dlen, TILE);
   const u32 per_tile = wbB + ceil_div(cs.dlen, DB);
-  const u32 dbase = dt * TILE + warp * GS;
-
-  const uint4* codes;
-  DomSrc src;
-  u32 cnt;
-  if (b < wbB) {
-    u32 lo = (A_BLOCKS + b) * DB;
-    cnt = min(DB, cs.wlen - lo);
-    codes = sd.whc + lo;
-    src = DomSrc{sd.win, nullptr, lo};
-  } else {
-    u32 lo = (b - wbB) * DB;
-    cnt = min(DB, cs.dlen - lo);
-    codes = sd.dhc + lo;
-    src = DomSrc{sd.pts, sd.dpos, lo};
-  }
-  if (!stage_block(codes, cnt, S, P)) return;
+  const u32 dbase = mt.tile * TILE + warp * GS;
+  const u32 cnt = mt.cnt;
+  const DomSrc src = mt.dense ? DomSrc{sd.pts, sd.dpos, mt.base} : DomSrc{sd.win, nullptr, mt.base};
   Cands c;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -545,7 +579,7 @@ __device__ void item_b(const Params& P, const SegDesc& sd, SegState* cur, SegSta
     load_cand<D>(sd, pos, valid, c, r);
   }
   if (__any_sync(FULL, any_alive(c))) {
-    scan_smem<D>(S.codes, cnt, src, sd.pts, c);
+    scan_smem<D>(staged, cnt, src, sd.pts, c);
 #pragma unroll
     for (int r = 0; r < R; ++r)
       if (c.was[r] && !c.alive[r]) sd.alive[c.pos[r]] = 0;
@@ -600,24 +634,25 @@ __device__ void item_b(const Params& P, const SegDesc& sd, SegState* cur, SegSta
 }
 
 template <int D>
-__device__ void run_item(int phase, const Params& P, const SegDesc& sd, SegState* cur, SegState* nxt, u32 s,
-                         u32 l, u32 tiles_s, u32 tgid_base, u32 round, Shared& S) {
-  // block-major numbering: item l = block * tiles + tile
-  u32 tile = l % tiles_s, b = l / tiles_s;
-  if (phase == 0) item_a<D>(P, sd, cur, nxt, s, tile, tgid_base + tile, round, S);
-  else item_b<D>(P, sd, cur, nxt, s, tile, b, tgid_base + tile, round, S);
+__device__ void run_item(int phase, const Params& P, const SegDesc& sd, SegState* cur, SegState* nxt, const Meta& m,
+                         const uint4* staged, u32 round, Shared& S) {
+  if (phase == 0) item_a<D>(P, sd, cur, nxt, m, staged, round, S);
+  else item_b<D>(P, sd, cur, nxt, m, staged, round, S);
 }
 
 __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
-  extern __shared__ u32 dyn[];
+  extern __shared__ __align__(128) unsigned char dyn[];
   __shared__ Shared S;
-  u32* s_items = dyn;                 // nseg + 1
-  u32* s_tiles = dyn + (P.nseg + 1);  // nseg + 1
+  const u32 DB = P.cfg.dom_block;
+  uint4* const buf0 = reinterpret_cast<uint4*>(dyn);  // two buffers of DB FP16 images
+  u32* s_items = reinterpret_cast<u32*>(dyn + 2 * (size_t)DB * 16);  // nseg + 1
+  u32* s_tiles = s_items + (P.nseg + 1);                             // nseg + 1
   const u32 nseg = P.nseg;
 
   if (threadIdx.x == 0) {
-    mbar_init(&S.bar);
-    S.bar_phase = 0;
+    mbar_init(&S.bar[0]);
+    mbar_init(&S.bar[1]);
+    S.bar_phase[0] = S.bar_phase[1] = 0;
     for (u32 s = blockIdx.x; s < nseg; s += gridDim.x) {
       SegState z;
       z.cur = 0;
@@ -652,29 +687,48 @@ __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
         else P.ctl[C_A0 + ((round + 1) & 1)] = 0;
       }
       u32* counter = P.ctl + (phase == 0 ? C_A0 : C_B0) + (round & 1);
-      for (;;) {
-        if (threadIdx.x == 0) S.item = atomicAdd(counter, 1u);
+      // software pipeline: while the CTA scans item k from one buffer,
+      // thread 0 has already taken item k + 1 and its bulk copy is filling
+      // the other buffer
+      if (threadIdx.x == 0) produce(P, phase, cur, s_items, s_tiles, total, counter, buf0, 0, S);
+      __syncthreads();
+      bool aborted = false;
+      for (u32 k = 0;; ++k) {
+        const int slot = k & 1;
+        const Meta m = S.meta[slot];
+        if (m.item >= total) break;
+        if (m.copied && !mbar_wait(&S.bar[slot], S.bar_phase[slot], P.err, P.ctl)) {
+          aborted = true;
+          break;
+        }
         __syncthreads();
-        const u32 it = S.item;
-        __syncthreads();
-        if (it >= total) break;
-        const u32 s = find_segment(s_items, nseg, it);
-        const SegDesc sd = P.segs[s];
-        const u32 tiles_s = s_tiles[s + 1] - s_tiles[s];
-        const u32 l = it - s_items[s];
+        if (threadIdx.x == 0) {
+          if (m.copied) S.bar_phase[slot] ^= 1u;
+          produce(P, phase, cur, s_items, s_tiles, total, counter, buf0 + (size_t)(slot ^ 1) * DB, slot ^ 1, S);
+        }
+        const SegDesc sd = P.segs[m.s];
+        const uint4* staged = buf0 + (size_t)slot * DB;
         switch (sd.d) {
-          case 1: run_item<1>(phase, P, sd, cur, nxt, s, l, tiles_s, s_tiles[s], round, S); break;
-          case 2: run_item<2>(phase, P, sd, cur, nxt, s, l, tiles_s, s_tiles[s], round, S); break;
-          case 3: run_item<3>(phase, P, sd, cur, nxt, s, l, tiles_s, s_tiles[s], round, S); break;
-          case 4: run_item<4>(phase, P, sd, cur, nxt, s, l, tiles_s, s_tiles[s], round, S); break;
-          case 5: run_item<5>(phase, P, sd, cur, nxt, s, l, tiles_s, s_tiles[s], round, S); break;
-          case 6: run_item<6>(phase, P, sd, cur, nxt, s, l, tiles_s, s_tiles[s], round, S); break;
-          case 7: run_item<7>(phase, P, sd, cur, nxt, s, l, tiles_s, s_tiles[s], round, S); break;
-          default: run_item<8>(phase, P, sd, cur, nxt, s, l, tiles_s, s_tiles[s], round, S); break;
+          case 1: run_item<1>(phase, P, sd, cur, nxt, m, staged, round, S); break;
+          case 2: run_item<2>(phase, P, sd, cur, nxt, m, staged, round, S); break;
+          case 3: run_item<3>(phase, P, sd, cur, nxt, m, staged, round, S); break;
+          case 4: run_item<4>(phase, P, sd, cur, nxt, m, staged, round, S); break;
+          case 5: run_item<5>(phase, P, sd, cur, nxt, m, staged, round, S); break;
+          case 6: run_item<6>(phase, P, sd, cur, nxt, m, staged, round, S); break;
+          case 7: run_item<7>(phase, P, sd, cur, nxt, m, staged, round, S); break;
+          default: run_item<8>(phase, P, sd, cur, nxt, m, staged, round, S); break;
         }
         if (threadIdx.x == 0) atomicAdd(P.ctl + C_PROGRESS, 1u);
-        if (ld_vol_u32(P.ctl + C_ABORT)) break;
+        __syncthreads();
+        if (ld_vol_u32(P.ctl + C_ABORT)) {
+          aborted = true;
+          // the copy of the prefetched item may still be in flight
+          const Meta mn = S.meta[slot ^ 1];
+          if (mn.item < total && mn.copied) mbar_wait(&S.bar[slot ^ 1], S.bar_phase[slot ^ 1], P.err, P.ctl);
+          break;
+        }
       }
+      if (aborted) return;
       if (!grid_barrier(P.ctl, P.err)) return;
     }
   }
@@ -708,7 +762,7 @@ cudaError_t engine_run(const SegDesc* segs_dev, u32 nseg, const EngineCfg& cfg, 
   P.tcap = w.tcap;
   P.ctl = w.ctl;
   P.err = err;
-  size_t smem = 2 * (size_t)(nseg + 1) * sizeof(u32);
+  size_t smem = 2 * (size_t)cfg.dom_block * sizeof(uint4) + 2 * (size_t)(nseg + 1) * sizeof(u32);
   cudaError_t e = cudaFuncSetAttribute(k_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;

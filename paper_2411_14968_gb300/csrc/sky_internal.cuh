@@ -207,6 +207,13 @@ struct SegState {
   u32 rounds;   // rounds completed
 };
 
+// Built-in defaults of the engine knobs (sky_params: 0 selects these).  A
+// short first chunk builds a window quickly; later chunks are 4x the window.
+constexpr u32 DEFAULT_CHUNK_MIN = 1024;
+constexpr u32 DEFAULT_CHUNK_MAX = 262144;
+constexpr u32 DEFAULT_ALPHA_X4 = 16;
+constexpr u32 DEFAULT_DOM_BLOCK = 1024;
+
 struct EngineCfg {
   u32 chunk_min, chunk_max, alpha_x4, dom_block;
 };

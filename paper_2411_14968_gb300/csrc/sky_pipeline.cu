@@ -250,11 +250,11 @@ sky_status validate(const float* points, u64 n, u32 d, const sky_params* pa, Pla
   pl->P = (u32)P;
   if (pl->rep && (u64)pl->P * pl->k > (1u << 22)) return bad("too many representatives");
   pl->pid_bits = bits_for(P);
-  pl->cfg.chunk_min = p.chunk_min ? p.chunk_min : 4096;
-  pl->cfg.chunk_max = p.chunk_max ? p.chunk_max : 65536;
+  pl->cfg.chunk_min = p.chunk_min ? p.chunk_min : DEFAULT_CHUNK_MIN;
+  pl->cfg.chunk_max = p.chunk_max ? p.chunk_max : DEFAULT_CHUNK_MAX;
   if (pl->cfg.chunk_max < pl->cfg.chunk_min) pl->cfg.chunk_max = pl->cfg.chunk_min;
-  pl->cfg.alpha_x4 = p.chunk_alpha_x4 ? p.chunk_alpha_x4 : 8;
-  pl->cfg.dom_block = p.dom_block ? p.dom_block : 1024;
+  pl->cfg.alpha_x4 = p.chunk_alpha_x4 ? p.chunk_alpha_x4 : DEFAULT_ALPHA_X4;
+  pl->cfg.dom_block = p.dom_block ? p.dom_block : DEFAULT_DOM_BLOCK;
   if (pl->cfg.dom_block % 32) return bad("dom_block must be a multiple of 32");
   if (pl->cfg.dom_block > engine_max_dom_block()) return bad("dom_block above the engine's maximum");
   if (pl->cfg.chunk_min > (1u << 24) || pl->cfg.chunk_max > (1u << 24)) return bad("chunk too large");

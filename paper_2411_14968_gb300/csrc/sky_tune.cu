@@ -5,9 +5,11 @@
 // times whole queries (CUDA events around the call on the context's stream)
 // and keeps the fastest.
 //
-// Search: coordinate descent from the built-in defaults.  For each knob in
-// turn every candidate value is tried with the others held at their best
-// values so far; two sweeps, within a trial budget.  Each candidate runs
+// Search: from the built-in defaults, a joint search over the chunk growth
+// factor and the first chunk length (the two knobs that interact most),
+// then coordinate descent: for each knob in turn every candidate value is
+// tried with the others held at their best values so far; two sweeps,
+// within a trial budget.  Each candidate runs
 // twice and counts its faster run (the first may pay for growing the
 // workspace).
 #include <cfloat>
@@ -45,15 +47,15 @@ extern "C" sky_status sky_autotune(sky_ctx* ctx, const float* points, uint64_t n
   const int timing_was = sky::ctx_timing(ctx);
   sky_set_timing(ctx, 1);
   sky_params cur = *params;
-  if (!cur.dom_block) cur.dom_block = 1024;
-  if (!cur.chunk_min) cur.chunk_min = 4096;
-  if (!cur.chunk_max) cur.chunk_max = 65536;
-  if (!cur.chunk_alpha_x4) cur.chunk_alpha_x4 = 8;
+  if (!cur.dom_block) cur.dom_block = sky::DEFAULT_DOM_BLOCK;
+  if (!cur.chunk_min) cur.chunk_min = sky::DEFAULT_CHUNK_MIN;
+  if (!cur.chunk_max) cur.chunk_max = sky::DEFAULT_CHUNK_MAX;
+  if (!cur.chunk_alpha_x4) cur.chunk_alpha_x4 = sky::DEFAULT_ALPHA_X4;
   const Knob knobs[] = {
+      {&sky_params::chunk_alpha_x4, {4, 8, 16, 32, 64}},
       {&sky_params::dom_block, {256, 512, 1024, 2048}},
-      {&sky_params::chunk_max, {8192, 16384, 32768, 65536, 131072, 262144}},
-      {&sky_params::chunk_alpha_x4, {2, 4, 8, 16}},
-      {&sky_params::chunk_min, {1024, 4096, 16384}},
+      {&sky_params::chunk_min, {256, 1024, 4096, 16384}},
+      {&sky_params::chunk_max, {16384, 65536, 262144, 1048576}},
   };
   uint32_t trials = 0;
   sky_status status = SKY_OK;
@@ -73,6 +75,22 @@ extern "C" sky_status sky_autotune(sky_ctx* ctx, const float* points, uint64_t n
   };
   double cur_ms = 0;
   status = measure(cur, &cur_ms);
+  // first a joint search over the two knobs that interact most (the chunk
+  // growth factor and the first chunk), then coordinate descent on all
+  for (uint32_t al : {8u, 16u, 32u})
+    for (uint32_t cm : {256u, 1024u, 4096u}) {
+      if (trials >= max_trials || status != SKY_OK) break;
+      if (cur.chunk_alpha_x4 == al && cur.chunk_min == cm) continue;
+      sky_params cand = cur;
+      cand.chunk_alpha_x4 = al;
+      cand.chunk_min = cm;
+      double ms = 0;
+      status = measure(cand, &ms);
+      if (status == SKY_OK && ms < cur_ms) {
+        cur = cand;
+        cur_ms = ms;
+      }
+    }
   for (int sweep = 0; sweep < 2 && status == SKY_OK; ++sweep) {
     bool changed = false;
     for (const Knob& k : knobs) {
