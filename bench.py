@@ -49,11 +49,7 @@ L2_FLUSH_BYTES = 256 << 20
 SM_COUNT = 152
 
 
-def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+from paper_2411_14968_gb300.replicas import dist_env  # noqa: E402
 
 
 class ClockSampler:
@@ -260,24 +256,15 @@ def gpu_arm(args, rank, world, local):
     import torch
     from paper_2411_14968_gb300 import datagen, native
 
+    from paper_2411_14968_gb300.replicas import Replicas, throughput
+
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    reps = Replicas(world, dev)
+    barrier, max_over_ranks = reps.barrier, reps.max_over_ranks
 
     x = datagen.anticorrelated(N, D, SEED)
     xt = torch.from_numpy(x).to(dev)
@@ -360,7 +347,7 @@ def gpu_arm(args, rank, world, local):
     clk = clocks.stop()
     total_s = max_over_ranks(sum(ms) / 1e3)
     pts_per_step = N * len(VARIANTS)
-    value = pts_per_step * args.steps * world / total_s
+    value = throughput(pts_per_step * args.steps, world, total_s)
 
     # one query at a time, every partition of a query in one launch
     ms_pq, acc_pq = timed(lambda a: step_each(persistent, a), max(1, args.steps))

@@ -1,5 +1,6 @@
 // Local-skyline engine: Algorithm 1 (SFS) run on every partition of
-// Algorithm 2 at once, in one persistent cooperative launch.
+// Algorithm 2 -- of every query of a batch -- at once, in one persistent
+// launch driven by a device-side work queue.
 //
 // Exactness rests on one fact: t is outside Sky(r) iff some point of r
 // dominates t, whether or not that point is in the skyline itself (a minimal
@@ -14,7 +15,7 @@
 // point of the window -- the skyline points of the earlier chunks -- has a
 // strictly lower score than every chunk point, and every skyline dominator of
 // a chunk point is either in the window or in the chunk itself.  A round has
-// two phases separated by a grid barrier:
+// two phases:
 //   A. every chunk point is tested against the first window block (the
 //      strongest, lowest-score skyline points); the survivors of each tile of
 //      the chunk are compacted into the segment's dense list;
@@ -23,7 +24,20 @@
 //      itself dominated by a window point that also dominates the candidate,
 //      so the dense list holds every chunk dominator that matters); the
 //      survivors are appended to the window.
-// The last tile of a segment plans the segment's next round.
+//
+// Work queue.  Segments advance through their rounds independently; there
+// is no grid-wide barrier.  A phase of a segment is a task of items (tile of
+// 8 warps x 32 lanes x R candidates, dominator block of DB points, numbered
+// block-major so the strongest window points run first).  Publishing a task
+// reserves a contiguous range of tickets with one 64-bit atomic (task index
+// and ticket range together, so both orders agree) and then marks the task
+// valid.  A CTA claims tickets one at a time and finds the task of its
+// ticket by binary search over the published tasks.  The CTA that completes
+// the last tile of a phase publishes the segment's next phase (or its next
+// round's phase A, or finishes the segment); when the last segment finishes,
+// the CTAs still waiting for tickets leave.  Segments of different sizes and
+// queries of a batch thus overlap freely, and a segment's long phase never
+// holds up the others.
 //
 // Dominance test.  Every point carries, next to its FP32 attributes, their
 // round-down FP16 images packed two per 32-bit word.  Round-down is monotone,
@@ -31,13 +45,13 @@
 // and cannot dominate t: the FP16 test rejects exactly, two attributes per
 // half2 compare, and only pairs it passes are tested in FP32 (Def. 1).
 //
-// Work items are (tile of 8 warps x 32 lanes x R candidates, dominator block
-// of DB points), numbered block-major so that the strongest window points run
-// first.  A CTA stages the block's FP16 images in shared memory with one
-// cp.async.bulk copy completing on an mbarrier; each warp scans it with
-// broadcast shared loads and leaves the item when a ballot shows all its
-// candidates dead.  Every wait (mbarrier, grid barrier) is bounded by
-// %globaltimer and reports ERR_TIMEOUT instead of hanging.
+// Pipeline.  Thread 0 of a CTA claims the next item while the CTA scans the
+// current one and starts the bulk copy (cp.async.bulk, completing on an
+// mbarrier) of the next item's dominator block into the second of two
+// shared-memory buffers; each warp scans the staged block with broadcast
+// shared loads and leaves the item when a ballot shows all its candidates
+// dead.  Every wait (mbarrier, waiting for a ticket's task) is bounded: it
+// gives up with ERR_TIMEOUT when no item anywhere has completed for WAIT_NS.
 #include <algorithm>
 #include <cuda_fp16.h>
 #include "sky_internal.cuh"
@@ -53,11 +67,11 @@ constexpr int GS = 32 * R;              // candidates per warp
 constexpr int TILE = WARPS * GS;        // candidates per tile (CTA item)
 constexpr u32 DBMAX = 2048;             // dominator block capacity (points)
 constexpr u32 A_BLOCKS = 1;             // window blocks of phase A
-constexpr u32 MAX_SEG = 4096;           // segments per launch (shared-memory prefix)
-constexpr u64 WAIT_NS = 4000000000ull;  // bound of every wait
+constexpr u64 WAIT_NS = 4000000000ull;  // bound of every wait (without progress)
 
-enum { C_A0 = 0, C_A1 = 1, C_B0 = 2, C_B1 = 3, C_BAR_COUNT = 4, C_BAR_GEN = 5, C_ABORT = 6, C_MAXROUND = 7,
-       C_PROGRESS = 8 };
+// Control words of a launch (zeroed by the host before it).  The queue word
+// is 64-bit: (tasks published << 32) | tickets reserved.
+enum { C_TICKET = 0, C_QUEUE = 2, C_LIVE = 4, C_FINISHED = 5, C_ABORT = 6, C_MAXROUND = 7, C_PROGRESS = 8 };
 
 __device__ __forceinline__ u64 globaltimer() {
   u64 t;
@@ -113,49 +127,6 @@ __device__ bool mbar_wait(u64* bar, u32 parity, u32* err, u32* ctl) {
 }
 // Generic-proxy writes of global memory made visible to later bulk copies.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
-
-// Grid-wide barrier of the cooperative launch.  The wait is bounded by
-// progress, not by its length: a CTA gives up (ERR_TIMEOUT, abort) only
-// after WAIT_NS in which no work item anywhere completed, so a long round
-// of a large input is not mistaken for a hang.
-__device__ bool grid_barrier(u32* ctl, u32* err) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    u32 gen = ld_vol_u32(ctl + C_BAR_GEN);
-    __threadfence();
-    fence_proxy_async();
-    u32 arrived = atomicAdd(ctl + C_BAR_COUNT, 1u);
-    bool ok = true;
-    if (arrived == gridDim.x - 1) {
-      atomicExch(ctl + C_BAR_COUNT, 0u);
-      __threadfence();
-      atomicAdd(ctl + C_BAR_GEN, 1u);
-    } else {
-      u64 t0 = globaltimer();
-      u32 seen = ld_vol_u32(ctl + C_PROGRESS);
-      while (ld_vol_u32(ctl + C_BAR_GEN) == gen) {
-        if (ld_vol_u32(ctl + C_ABORT)) { ok = false; break; }
-        const u32 now = ld_vol_u32(ctl + C_PROGRESS);
-        if (now != seen) {
-          seen = now;
-          t0 = globaltimer();
-        }
-        if (globaltimer() - t0 > WAIT_NS) {
-          atomicOr(err, ERR_TIMEOUT);
-          atomicExch(ctl + C_ABORT, 1u);
-          ok = false;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    s_ok = ok && !ld_vol_u32(ctl + C_ABORT);
-  }
-  __syncthreads();
-  return s_ok;
-}
 
 // ------------------------------------------------------------ dominance test
 
@@ -281,20 +252,37 @@ __device__ __forceinline__ bool any_alive(const Cands& c) {
 
 __device__ __forceinline__ u32 ceil_div(u32 a, u32 b) { return (a + b - 1) / b; }
 
-// ------------------------------------------------------------ rounds
+// ------------------------------------------------------------ work queue
+
+struct Task {
+  u32 s;        // segment
+  u32 phase;    // 0: A, 1: B
+  u32 tiles;    // candidate tiles of the phase
+  u32 items;    // work items (tiles x dominator blocks)
+  u32 ticket0;  // first ticket of the task
+  u32 valid;    // written last
+  u32 pad[2];
+};
 
 struct Params {
   const SegDesc* segs;
   u32 nseg;
   EngineCfg cfg;
-  SegState* st;        // 2 * nseg
-  u32* done_round;     // nseg
-  u32* tdoneA;         // per tile of phase A (capacity tcap)
-  u32* tdoneB;         // per tile of phase B (capacity tcap)
+  SegState* st;    // nseg
+  u32* tbase;      // nseg: first completion counter of each segment
+  u32* tdoneA;     // completion counters of phase-A tiles (capacity tcap)
+  u32* tdoneB;     // completion counters of phase-B tiles (capacity tcap)
   u64 tcap;
+  Task* tasks;     // task_cap entries, valid flags zero before the launch
+  u32 task_cap;
   u32* ctl;
   u32* err;
 };
+
+__device__ __forceinline__ void abort_launch(const Params& P, u32 code) {
+  atomicOr(P.err, code);
+  atomicExch(P.ctl + C_ABORT, 1u);
+}
 
 __device__ __forceinline__ u32 upper_bound_score(const float* __restrict__ score, u32 from, u32 n, float v) {
   u32 lo = from, hi = n;
@@ -306,8 +294,10 @@ __device__ __forceinline__ u32 upper_bound_score(const float* __restrict__ score
   return lo;
 }
 
-// Next chunk of a segment: nominal length from the window size, extended to
-// the end of a run of equal scores.
+// Next chunk of a segment: nominal length alpha/4 x the window size, and at
+// least an eighth of the points already processed (so a segment whose window
+// stays small still needs only logarithmically many rounds), clamped, then
+// extended to the end of a run of equal scores.
 __device__ void plan_round(const SegDesc& sd, const EngineCfg& cfg, SegState& s) {
   s.dlen = 0;
   s.done_a = 0;
@@ -318,6 +308,7 @@ __device__ void plan_round(const SegDesc& sd, const EngineCfg& cfg, SegState& s)
     return;
   }
   u64 k = ((u64)s.wlen * cfg.alpha_x4) / 4;
+  if (k < s.cur / 8) k = s.cur / 8;
   k = k < cfg.chunk_min ? cfg.chunk_min : k;
   k = k > cfg.chunk_max ? cfg.chunk_max : k;
   u64 e = (u64)s.cur + k;
@@ -326,23 +317,92 @@ __device__ void plan_round(const SegDesc& sd, const EngineCfg& cfg, SegState& s)
   s.tiles = ceil_div(s.cend - s.cur, TILE);
 }
 
-__device__ __forceinline__ u32 items_a(const SegState& s, u32 DB) {
-  u32 wb = ceil_div(s.wlen, DB);
-  return s.tiles * max(1u, min(wb, A_BLOCKS));
-}
-__device__ __forceinline__ u32 dtiles_of(const SegState& s) { return ceil_div(s.dlen, TILE); }
-__device__ __forceinline__ u32 items_b(const SegState& s, u32 DB) {
-  u32 wb = ceil_div(s.wlen, DB);
-  u32 wbB = wb > A_BLOCKS ? wb - A_BLOCKS : 0;
-  return dtiles_of(s) * (wbB + ceil_div(s.dlen, DB));
+// Publishes a task (one thread).  The 64-bit atomic reserves the task index
+// and its ticket range together.
+__device__ void publish(const Params& P, u32 s, u32 phase, u32 tiles, u32 items) {
+  unsigned long long* q = reinterpret_cast<unsigned long long*>(P.ctl + C_QUEUE);
+  const u64 old = atomicAdd(q, (1ull << 32) | (u64)items);
+  const u32 idx = (u32)(old >> 32), t0 = (u32)old;
+  if (idx >= P.task_cap || (u64)t0 + items >= 0xffff0000ull) {
+    abort_launch(P, ERR_CAPACITY);
+    return;
+  }
+  Task* t = P.tasks + idx;
+  t->s = s;
+  t->phase = phase;
+  t->tiles = tiles;
+  t->items = items;
+  t->ticket0 = t0;
+  __threadfence();
+  *(volatile u32*)&t->valid = 1u;
 }
 
+__device__ void finish_segment(const Params& P) {
+  __threadfence();
+  if (atomicSub(P.ctl + C_LIVE, 1u) == 1u) {
+    __threadfence();
+    atomicExch(P.ctl + C_FINISHED, 1u);
+  }
+}
+
+// Plans segment s's next round from nx (cur, wlen, rounds set) and publishes
+// its phase A, or finishes the segment.
+__device__ void start_round(const Params& P, const SegDesc& sd, u32 s, SegState nx) {
+  nx.wfill = nx.wlen;
+  plan_round(sd, P.cfg, nx);
+  P.st[s] = nx;
+  atomicMax(P.ctl + C_MAXROUND, nx.rounds);
+  if (nx.tiles == 0) {
+    finish_segment(P);
+    return;
+  }
+  __threadfence();
+  const u32 per_tile = max(1u, min(ceil_div(nx.wlen, P.cfg.dom_block), A_BLOCKS));
+  publish(P, s, 0, nx.tiles, nx.tiles * per_tile);
+}
+
+__device__ __forceinline__ u32 task_valid(const Task* t) { return *(const volatile u32*)&t->valid; }
+
+// Finds the task of ticket t: 1 found (*idx), 0 not known yet (retry), -1
+// no more work.  `cursor` is the task of the CTA's previous ticket, a lower
+// bound because a CTA's tickets increase.
+__device__ int find_task(const Params& P, u32 t, u32* cursor, u32* idx_out) {
+  const volatile unsigned long long* q = reinterpret_cast<const volatile unsigned long long*>(P.ctl + C_QUEUE);
+  u64 qv = *q;
+  if (t >= (u32)qv) {
+    if (!ld_vol_u32(P.ctl + C_FINISHED)) return 0;
+    __threadfence();
+    qv = *q;  // nothing is published once every segment has finished
+    if (t >= (u32)qv) return -1;
+  }
+  u32 lo = *cursor, hi = (u32)(qv >> 32);
+  if (hi > P.task_cap) hi = P.task_cap;
+  while (hi - lo > 1) {
+    const u32 mid = (lo + hi) >> 1;
+    const Task* tm = P.tasks + mid;
+    if (!task_valid(tm)) return 0;
+    __threadfence();
+    if (__ldcg(&tm->ticket0) <= t) lo = mid;
+    else hi = mid;
+  }
+  if (!task_valid(P.tasks + lo)) return 0;
+  __threadfence();
+  *cursor = lo;
+  *idx_out = lo;
+  return 1;
+}
+
+// ------------------------------------------------------------ items
+
 // One work item as the producer thread planned it.
+enum : u32 { M_EMPTY = 0, M_PENDING = 1, M_READY = 2, M_DONE = 3 };
 struct Meta {
-  u32 item;    // item index of the phase (>= total: no item)
+  u32 state;
+  u32 ticket;
   u32 s;       // segment
+  u32 phase;
   u32 tile;    // candidate tile (phase A) or dense-list tile (phase B)
-  u32 tgid;    // global tile id (completion counters)
+  u32 tgid;    // completion counter of the tile
   u32 cnt;     // dominators staged in the item's buffer
   u32 base;    // index of the first staged dominator in its source
   u32 dense;   // 1: the dominators are dense-list points (FP32 via dpos)
@@ -353,110 +413,69 @@ struct Shared {
   Meta meta[2];
   u64 bar[2];
   u32 bar_phase[2];
+  u32 cursor;
   u32 flag;
-  u32 warp_tot[WARPS];
-  u32 carry;
 };
 
-// Exclusive prefix over segments of the item count (phase 0: A, 1: B) and
-// of the tile count, into out_items / out_tiles [nseg + 1].
-__device__ void prefix_segments(const Params& P, const SegState* cur, u32 round, int phase, u32* out_items,
-                                u32* out_tiles, Shared& S) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// Producer (thread 0 only, never blocks): claims a ticket for buffer `slot`
+// if it has none, and once the ticket's task is known plans the item and
+// starts the bulk copy of its dominator block's FP16 images.  The buffer is
+// free: every warp has finished the item that used it.
+__device__ void produce(const Params& P, Shared& S, int slot, uint4* buf) {
+  Meta& m = S.meta[slot];
+  if (m.state == M_EMPTY) {
+    m.ticket = atomicAdd(P.ctl + C_TICKET, 1u);
+    m.state = M_PENDING;
+  }
+  if (m.state != M_PENDING) return;
+  u32 idx = 0;
+  const int f = find_task(P, m.ticket, &S.cursor, &idx);
+  if (f < 0) {
+    m.state = M_DONE;
+    return;
+  }
+  if (f == 0) return;
+  const Task* tk = P.tasks + idx;
   const u32 DB = P.cfg.dom_block;
-  for (int pass = 0; pass < 2; ++pass) {
-    u32* out = pass == 0 ? out_items : out_tiles;
-    if (threadIdx.x == 0) S.carry = 0;
-    __syncthreads();
-    for (u32 base = 0; base < P.nseg; base += THREADS) {
-      u32 i = base + threadIdx.x;
-      u32 v = 0;
-      if (i < P.nseg && ld_cg_u32(P.done_round + i) > round) {
-        SegState s;
-        s.wlen = ld_cg_u32(&cur[i].wlen);
-        s.tiles = ld_cg_u32(&cur[i].tiles);
-        s.dlen = ld_cg_u32(&cur[i].dlen);
-        if (phase == 0) v = pass == 0 ? items_a(s, DB) : s.tiles;
-        else v = pass == 0 ? items_b(s, DB) : dtiles_of(s);
-      }
-      u32 x = v;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        u32 y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
-      }
-      if (lane == 31) S.warp_tot[warp] = x;
-      __syncthreads();
-      u32 pre = S.carry;
-      for (int w2 = 0; w2 < warp; ++w2) pre += S.warp_tot[w2];
-      if (i < P.nseg) out[i] = pre + x - v;
-      __syncthreads();
-      if (threadIdx.x == THREADS - 1) S.carry = pre + x;
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) out[P.nseg] = S.carry;
-    __syncthreads();
-  }
-}
-
-__device__ __forceinline__ u32 find_segment(const u32* pre, u32 nseg, u32 it) {
-  u32 lo = 0, hi = nseg;
-  while (hi - lo > 1) {
-    u32 mid = (lo + hi) >> 1;
-    if (pre[mid] <= it) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
-
-// Producer (thread 0 only): takes the next item of the phase and starts the
-// bulk copy of its dominator block's FP16 images into buffer `slot`.  The
-// buffer is free: every warp has passed the end of the item that used it.
-__device__ void produce(const Params& P, int phase, const SegState* cur, const u32* s_items, const u32* s_tiles,
-                        u32 total, u32* counter, uint4* buf, int slot, Shared& S) {
-  Meta m;
-  m.item = atomicAdd(counter, 1u);
-  m.copied = 0;
-  m.cnt = 0;
-  if (m.item < total) {
-    const u32 DB = P.cfg.dom_block;
-    m.s = find_segment(s_items, P.nseg, m.item);
-    const u32 l = m.item - s_items[m.s];
-    const u32 tiles_s = s_tiles[m.s + 1] - s_tiles[m.s];
-    m.tile = l % tiles_s;  // block-major numbering: item l = block * tiles + tile
-    const u32 b = l / tiles_s;
-    m.tgid = s_tiles[m.s] + m.tile;
-    const u32 wlen = ld_cg_u32(&cur[m.s].wlen);
-    const uint4* codes;
-    if (phase == 0) {
-      m.cnt = min(wlen, DB);
-      m.base = 0;
+  m.s = __ldcg(&tk->s);
+  m.phase = __ldcg(&tk->phase);
+  const u32 tiles = __ldcg(&tk->tiles);
+  const u32 l = m.ticket - __ldcg(&tk->ticket0);
+  m.tile = l % tiles;  // block-major: item l = block * tiles + tile
+  const u32 b = l / tiles;
+  m.tgid = __ldcg(P.tbase + m.s) + m.tile;
+  const u32 wlen = ld_cg_u32(&P.st[m.s].wlen);
+  const SegDesc* sd = P.segs + m.s;
+  const uint4* codes;
+  if (m.phase == 0) {
+    m.cnt = min(wlen, DB);
+    m.base = 0;
+    m.dense = 0;
+    codes = sd->whc;
+  } else {
+    const u32 dlen = ld_cg_u32(&P.st[m.s].dlen);
+    const u32 wb = ceil_div(wlen, DB);
+    const u32 wbB = wb > A_BLOCKS ? wb - A_BLOCKS : 0;
+    if (b < wbB) {
+      m.base = (A_BLOCKS + b) * DB;
+      m.cnt = min(DB, wlen - m.base);
       m.dense = 0;
-      codes = P.segs[m.s].whc;
+      codes = sd->whc + m.base;
     } else {
-      const u32 dlen = ld_cg_u32(&cur[m.s].dlen);
-      const u32 wb = ceil_div(wlen, DB);
-      const u32 wbB = wb > A_BLOCKS ? wb - A_BLOCKS : 0;
-      if (b < wbB) {
-        m.base = (A_BLOCKS + b) * DB;
-        m.cnt = min(DB, wlen - m.base);
-        m.dense = 0;
-        codes = P.segs[m.s].whc + m.base;
-      } else {
-        m.base = (b - wbB) * DB;
-        m.cnt = min(DB, dlen - m.base);
-        m.dense = 1;
-        codes = P.segs[m.s].dhc + m.base;
-      }
-    }
-    if (m.cnt) {
-      fence_proxy_async();
-      mbar_expect_tx(&S.bar[slot], m.cnt * 16u);
-      bulk_g2s(buf, codes, m.cnt * 16u, &S.bar[slot]);
-      m.copied = 1;
+      m.base = (b - wbB) * DB;
+      m.cnt = min(DB, dlen - m.base);
+      m.dense = 1;
+      codes = sd->dhc + m.base;
     }
   }
-  S.meta[slot] = m;
+  m.copied = 0;
+  if (m.cnt) {
+    fence_proxy_async();
+    mbar_expect_tx(&S.bar[slot], m.cnt * 16u);
+    bulk_g2s(buf, codes, m.cnt * 16u, &S.bar[slot]);
+    m.copied = 1;
+  }
+  m.state = M_READY;
 }
 
 template <int D>
@@ -470,16 +489,17 @@ __device__ void load_cand(const SegDesc& sd, u32 pos, bool valid, Cands& c, int 
 
 // Phase A item: tile `tile` of the chunk against window block 0.
 template <int D>
-__device__ void item_a(const Params& P, const SegDesc& sd, SegState* cur, SegState* nxt, const Meta& mt,
-                       const uint4* staged, u32 round, Shared& S) {
+__device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const uint4* staged, Shared& S) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 DB = P.cfg.dom_block;
-  const u32 s = mt.s, tgid = mt.tgid;
+  const u32 s = mt.s;
+  SegState* st = P.st + s;
   SegState cs;
-  cs.cur = ld_cg_u32(&cur[s].cur);
-  cs.cend = ld_cg_u32(&cur[s].cend);
-  cs.wlen = ld_cg_u32(&cur[s].wlen);
-  cs.tiles = ld_cg_u32(&cur[s].tiles);
+  cs.cur = ld_cg_u32(&st->cur);
+  cs.cend = ld_cg_u32(&st->cend);
+  cs.wlen = ld_cg_u32(&st->wlen);
+  cs.tiles = ld_cg_u32(&st->tiles);
+  cs.rounds = ld_cg_u32(&st->rounds);
   const u32 cnt = mt.cnt;
   const u32 per_tile = max(1u, min(ceil_div(cs.wlen, DB), A_BLOCKS));
   const u32 gbase = cs.cur + mt.tile * TILE + warp * GS;
@@ -502,9 +522,9 @@ __device__ void item_a(const Params& P, const SegDesc& sd, SegState* cur, SegSta
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    u32 old = atomicAdd(P.tdoneA + tgid, 1u);
+    u32 old = atomicAdd(P.tdoneA + mt.tgid, 1u);
     S.flag = (old == per_tile - 1);
-    if (S.flag) P.tdoneA[tgid] = 0;
+    if (S.flag) P.tdoneA[mt.tgid] = 0;
   }
   __syncthreads();
   if (!S.flag) return;
@@ -516,7 +536,7 @@ __device__ void item_a(const Params& P, const SegDesc& sd, SegState* cur, SegSta
     bool a = pos < cs.cend && ld_cg_u8(sd.alive + pos);
     u32 m = __ballot_sync(FULL, a);
     u32 base = 0;
-    if (lane == 0 && m) base = atomicAdd(&cur[s].dlen, (u32)__popc(m));
+    if (lane == 0 && m) base = atomicAdd(&st->dlen, (u32)__popc(m));
     base = __shfl_sync(FULL, base, 0);
     if (a) {
       u32 slot = base + __popc(m & ((1u << lane) - 1u));
@@ -528,41 +548,42 @@ __device__ void item_a(const Params& P, const SegDesc& sd, SegState* cur, SegSta
   fence_proxy_async();
   __syncthreads();
   if (threadIdx.x == 0) {
-    u32 old = atomicAdd(&cur[s].done_a, 1u);
+    u32 old = atomicAdd(&st->done_a, 1u);
     if (old == cs.tiles - 1) {
+      // last tile of phase A: publish phase B, or the next round if nothing
+      // survived
       __threadfence();
-      u32 dl = atomicAdd(&cur[s].dlen, 0u);
+      const u32 dl = atomicAdd(&st->dlen, 0u);
       if (dl == 0) {
-        // nothing survived phase A: the next round starts now
         SegState nx;
         nx.cur = cs.cend;
-        nx.wlen = ld_cg_u32(&cur[s].wlen);
-        nx.wfill = nx.wlen;
-        nx.rounds = ld_cg_u32(&cur[s].rounds) + 1;
-        plan_round(sd, P.cfg, nx);
-        nxt[s] = nx;
-        if (nx.tiles == 0) P.done_round[s] = round + 1;
-        atomicMax(P.ctl + C_MAXROUND, nx.rounds);
+        nx.wlen = cs.wlen;
+        nx.rounds = cs.rounds + 1;
+        start_round(P, sd, s, nx);
+      } else {
+        const u32 wb = ceil_div(cs.wlen, DB);
+        const u32 wbB = wb > A_BLOCKS ? wb - A_BLOCKS : 0;
+        const u32 dtiles = ceil_div(dl, TILE);
+        publish(P, s, 1, dtiles, dtiles * (wbB + ceil_div(dl, DB)));
       }
     }
   }
 }
 
-// Phase B item: dense tile `dt` against window block A_BLOCKS + b, or dense
-// block b - (window blocks of phase B).
+// Phase B item: dense tile against window block A_BLOCKS + b, or dense block
+// b - (window blocks of phase B).
 template <int D>
-__device__ void item_b(const Params& P, const SegDesc& sd, SegState* cur, SegState* nxt, const Meta& mt,
-                       const uint4* staged, u32 round, Shared& S) {
+__device__ void item_b(const Params& P, const SegDesc& sd, const Meta& mt, const uint4* staged, Shared& S) {
   constexpr int V = vec_of(D);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 DB = P.cfg.dom_block;
-  const u32 s = mt.s, tgid = mt.tgid;
+  const u32 s = mt.s;
+  SegState* st = P.st + s;
   SegState cs;
-  cs.cur = ld_cg_u32(&cur[s].cur);
-  cs.cend = ld_cg_u32(&cur[s].cend);
-  cs.wlen = ld_cg_u32(&cur[s].wlen);
-  cs.dlen = ld_cg_u32(&cur[s].dlen);
-  cs.rounds = ld_cg_u32(&cur[s].rounds);
+  cs.cend = ld_cg_u32(&st->cend);
+  cs.wlen = ld_cg_u32(&st->wlen);
+  cs.dlen = ld_cg_u32(&st->dlen);
+  cs.rounds = ld_cg_u32(&st->rounds);
   const u32 wb = ceil_div(cs.wlen, DB);
   const u32 wbB = wb > A_BLOCKS ? wb - A_BLOCKS : 0;
   const u32 dtiles = ceil_div(cs.dlen, TILE);
@@ -578,7 +599,7 @@ __device__ void item_b(const Params& P, const SegDesc& sd, SegState* cur, SegSta
     u32 pos = valid ? __ldcg(sd.dpos + e) : 0;
     load_cand<D>(sd, pos, valid, c, r);
   }
-  if (__any_sync(FULL, any_alive(c))) {
+  if (cnt && __any_sync(FULL, any_alive(c))) {
     scan_smem<D>(staged, cnt, src, sd.pts, c);
 #pragma unroll
     for (int r = 0; r < R; ++r)
@@ -587,9 +608,9 @@ __device__ void item_b(const Params& P, const SegDesc& sd, SegState* cur, SegSta
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    u32 old = atomicAdd(P.tdoneB + tgid, 1u);
+    u32 old = atomicAdd(P.tdoneB + mt.tgid, 1u);
     S.flag = (old == per_tile - 1);
-    if (S.flag) P.tdoneB[tgid] = 0;
+    if (S.flag) P.tdoneB[mt.tgid] = 0;
   }
   __syncthreads();
   if (!S.flag) return;
@@ -602,7 +623,7 @@ __device__ void item_b(const Params& P, const SegDesc& sd, SegState* cur, SegSta
     bool a = e < cs.dlen && ld_cg_u8(sd.alive + pos);
     u32 m = __ballot_sync(FULL, a);
     u32 base = 0;
-    if (lane == 0 && m) base = atomicAdd(&cur[s].wfill, (u32)__popc(m));
+    if (lane == 0 && m) base = atomicAdd(&st->wfill, (u32)__popc(m));
     base = __shfl_sync(FULL, base, 0);
     if (a) {
       u32 slot = base + __popc(m & ((1u << lane) - 1u));
@@ -617,27 +638,70 @@ __device__ void item_b(const Params& P, const SegDesc& sd, SegState* cur, SegSta
   fence_proxy_async();
   __syncthreads();
   if (threadIdx.x == 0) {
-    u32 old = atomicAdd(&cur[s].done_b, 1u);
+    u32 old = atomicAdd(&st->done_b, 1u);
     if (old == dtiles - 1) {
+      // last dense tile: the next round
       __threadfence();
       SegState nx;
       nx.cur = cs.cend;
-      nx.wlen = atomicAdd(&cur[s].wfill, 0u);
-      nx.wfill = nx.wlen;
+      nx.wlen = atomicAdd(&st->wfill, 0u);
       nx.rounds = cs.rounds + 1;
-      plan_round(sd, P.cfg, nx);
-      nxt[s] = nx;
-      if (nx.tiles == 0) P.done_round[s] = round + 1;
-      atomicMax(P.ctl + C_MAXROUND, nx.rounds);
+      start_round(P, sd, s, nx);
     }
   }
 }
 
 template <int D>
-__device__ void run_item(int phase, const Params& P, const SegDesc& sd, SegState* cur, SegState* nxt, const Meta& m,
-                         const uint4* staged, u32 round, Shared& S) {
-  if (phase == 0) item_a<D>(P, sd, cur, nxt, m, staged, round, S);
-  else item_b<D>(P, sd, cur, nxt, m, staged, round, S);
+__device__ void run_item(const Params& P, const SegDesc& sd, const Meta& m, const uint4* staged, Shared& S) {
+  if (m.phase == 0) item_a<D>(P, sd, m, staged, S);
+  else item_b<D>(P, sd, m, staged, S);
+}
+
+// Prologue of CTA 0: completion-counter bases of the segments, then round 0
+// of every segment (published or finished at once).
+__device__ bool prologue(const Params& P) {
+  __shared__ u32 s_carry;
+  __shared__ u32 s_warp[WARPS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (u32 base = 0; base < P.nseg; base += THREADS) {
+    const u32 i = base + threadIdx.x;
+    // a phase of segment i has at most ceil(n / TILE) tiles
+    const u32 v = i < P.nseg ? ceil_div(P.segs[i].n, TILE) + 1 : 0;
+    u32 x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      u32 y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    u32 pre = s_carry;
+    for (int w2 = 0; w2 < warp; ++w2) pre += s_warp[w2];
+    if (i < P.nseg) P.tbase[i] = pre + x - v;
+    __syncthreads();
+    if (threadIdx.x == THREADS - 1) s_carry = pre + x;
+    __syncthreads();
+  }
+  if (s_carry > P.tcap) {
+    if (threadIdx.x == 0) abort_launch(P, ERR_CAPACITY);
+    return false;
+  }
+  if (threadIdx.x == 0) {
+    P.ctl[C_LIVE] = P.nseg;
+    if (P.nseg == 0) P.ctl[C_FINISHED] = 1;
+  }
+  __threadfence();
+  __syncthreads();
+  for (u32 i = threadIdx.x; i < P.nseg; i += THREADS) {
+    SegState z;
+    z.cur = 0;
+    z.wlen = 0;
+    z.rounds = 0;
+    start_round(P, P.segs[i], i, z);
+  }
+  return true;
 }
 
 __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
@@ -645,91 +709,73 @@ __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
   __shared__ Shared S;
   const u32 DB = P.cfg.dom_block;
   uint4* const buf0 = reinterpret_cast<uint4*>(dyn);  // two buffers of DB FP16 images
-  u32* s_items = reinterpret_cast<u32*>(dyn + 2 * (size_t)DB * 16);  // nseg + 1
-  u32* s_tiles = s_items + (P.nseg + 1);                             // nseg + 1
-  const u32 nseg = P.nseg;
 
   if (threadIdx.x == 0) {
     mbar_init(&S.bar[0]);
     mbar_init(&S.bar[1]);
     S.bar_phase[0] = S.bar_phase[1] = 0;
-    for (u32 s = blockIdx.x; s < nseg; s += gridDim.x) {
-      SegState z;
-      z.cur = 0;
-      z.wlen = 0;
-      z.wfill = 0;
-      z.rounds = 0;
-      plan_round(P.segs[s], P.cfg, z);
-      P.st[s] = z;
-      P.st[nseg + s] = z;
-      P.done_round[s] = z.tiles ? 0xffffffffu : 0u;
-    }
+    S.cursor = 0;
+    S.meta[0].state = M_EMPTY;
+    S.meta[1].state = M_EMPTY;
   }
-  if (!grid_barrier(P.ctl, P.err)) return;
+  __syncthreads();
+  if (blockIdx.x == 0 && !prologue(P)) return;
 
-  for (u32 round = 0;; ++round) {
-    SegState* cur = P.st + (round & 1) * nseg;
-    SegState* nxt = P.st + ((round + 1) & 1) * nseg;
-    for (int phase = 0; phase < 2; ++phase) {
-      prefix_segments(P, cur, round, phase, s_items, s_tiles, S);
-      const u32 total = s_items[nseg];
-      if (phase == 0 && total == 0) return;  // every segment is done
-      if (s_tiles[nseg] > P.tcap) {
-        if (threadIdx.x == 0) {
-          atomicOr(P.err, ERR_CAPACITY);
-          atomicExch(P.ctl + C_ABORT, 1u);
-        }
-        return;
-      }
-      // the counter of the next phase is idle now: clear it
-      if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (phase == 0) P.ctl[C_B0 + (round & 1)] = 0;
-        else P.ctl[C_A0 + ((round + 1) & 1)] = 0;
-      }
-      u32* counter = P.ctl + (phase == 0 ? C_A0 : C_B0) + (round & 1);
-      // software pipeline: while the CTA scans item k from one buffer,
-      // thread 0 has already taken item k + 1 and its bulk copy is filling
-      // the other buffer
-      if (threadIdx.x == 0) produce(P, phase, cur, s_items, s_tiles, total, counter, buf0, 0, S);
-      __syncthreads();
-      bool aborted = false;
-      for (u32 k = 0;; ++k) {
-        const int slot = k & 1;
-        const Meta m = S.meta[slot];
-        if (m.item >= total) break;
-        if (m.copied && !mbar_wait(&S.bar[slot], S.bar_phase[slot], P.err, P.ctl)) {
-          aborted = true;
-          break;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          if (m.copied) S.bar_phase[slot] ^= 1u;
-          produce(P, phase, cur, s_items, s_tiles, total, counter, buf0 + (size_t)(slot ^ 1) * DB, slot ^ 1, S);
-        }
-        const SegDesc sd = P.segs[m.s];
-        const uint4* staged = buf0 + (size_t)slot * DB;
-        switch (sd.d) {
-          case 1: run_item<1>(phase, P, sd, cur, nxt, m, staged, round, S); break;
-          case 2: run_item<2>(phase, P, sd, cur, nxt, m, staged, round, S); break;
-          case 3: run_item<3>(phase, P, sd, cur, nxt, m, staged, round, S); break;
-          case 4: run_item<4>(phase, P, sd, cur, nxt, m, staged, round, S); break;
-          case 5: run_item<5>(phase, P, sd, cur, nxt, m, staged, round, S); break;
-          case 6: run_item<6>(phase, P, sd, cur, nxt, m, staged, round, S); break;
-          case 7: run_item<7>(phase, P, sd, cur, nxt, m, staged, round, S); break;
-          default: run_item<8>(phase, P, sd, cur, nxt, m, staged, round, S); break;
-        }
-        if (threadIdx.x == 0) atomicAdd(P.ctl + C_PROGRESS, 1u);
-        __syncthreads();
+  if (threadIdx.x == 0) produce(P, S, 0, buf0);
+  for (u32 k = 0;; ++k) {
+    const int slot = k & 1;
+    uint4* const cur_buf = buf0 + (size_t)slot * DB;
+    // wait until the slot's ticket has a task (or there is no more work)
+    if (threadIdx.x == 0) {
+      u64 t0 = 0;
+      u32 seen = 0;
+      while (S.meta[slot].state == M_PENDING) {
+        produce(P, S, slot, cur_buf);
+        if (S.meta[slot].state != M_PENDING) break;
         if (ld_vol_u32(P.ctl + C_ABORT)) {
-          aborted = true;
-          // the copy of the prefetched item may still be in flight
-          const Meta mn = S.meta[slot ^ 1];
-          if (mn.item < total && mn.copied) mbar_wait(&S.bar[slot ^ 1], S.bar_phase[slot ^ 1], P.err, P.ctl);
+          S.meta[slot].state = M_DONE;
           break;
         }
+        const u32 now = ld_vol_u32(P.ctl + C_PROGRESS);
+        if (t0 == 0 || now != seen) {
+          seen = now;
+          t0 = globaltimer();
+        } else if (globaltimer() - t0 > WAIT_NS) {
+          abort_launch(P, ERR_TIMEOUT);
+          S.meta[slot].state = M_DONE;
+          break;
+        }
+        __nanosleep(128);
       }
-      if (aborted) return;
-      if (!grid_barrier(P.ctl, P.err)) return;
+    }
+    __syncthreads();
+    const Meta m = S.meta[slot];
+    if (m.state != M_READY) break;
+    if (m.copied && !mbar_wait(&S.bar[slot], S.bar_phase[slot], P.err, P.ctl)) break;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (m.copied) S.bar_phase[slot] ^= 1u;
+      S.meta[slot].state = M_EMPTY;
+      produce(P, S, slot ^ 1, buf0 + (size_t)(slot ^ 1) * DB);
+    }
+    const SegDesc sd = P.segs[m.s];
+    switch (sd.d) {
+      case 1: run_item<1>(P, sd, m, cur_buf, S); break;
+      case 2: run_item<2>(P, sd, m, cur_buf, S); break;
+      case 3: run_item<3>(P, sd, m, cur_buf, S); break;
+      case 4: run_item<4>(P, sd, m, cur_buf, S); break;
+      case 5: run_item<5>(P, sd, m, cur_buf, S); break;
+      case 6: run_item<6>(P, sd, m, cur_buf, S); break;
+      case 7: run_item<7>(P, sd, m, cur_buf, S); break;
+      default: run_item<8>(P, sd, m, cur_buf, S); break;
+    }
+    if (threadIdx.x == 0) atomicAdd(P.ctl + C_PROGRESS, 1u);
+    __syncthreads();
+    if (ld_vol_u32(P.ctl + C_ABORT)) {
+      // the copy of the prefetched item may still be in flight
+      const Meta mn = S.meta[slot ^ 1];
+      if (mn.state == M_READY && mn.copied) mbar_wait(&S.bar[slot ^ 1], S.bar_phase[slot ^ 1], P.err, P.ctl);
+      break;
     }
   }
 }
@@ -738,31 +784,33 @@ int g_sms = 0;
 
 }  // namespace
 
-u64 engine_tile_capacity(u64 total_points, u32 nseg) { return total_points / TILE + nseg + 1; }
+u64 engine_tile_capacity(u64 total_points, u32 nseg) { return total_points / TILE + 2ull * nseg + 1; }
+
+u64 engine_task_capacity(u64 total_points, u32 nseg, u32 chunk_min) {
+  // every round but a segment's last processes at least chunk_min points,
+  // and a round publishes at most two tasks
+  return 2 * (total_points / (chunk_min ? chunk_min : 1) + 2ull * nseg) + 16;
+}
 
 cudaError_t engine_run(const SegDesc* segs_dev, u32 nseg, const EngineCfg& cfg, const EngineWork& w, u32* err,
                        cudaStream_t st) {
   if (nseg == 0) return cudaSuccess;
-  if (nseg > MAX_SEG) {
-    for (u32 s0 = 0; s0 < nseg; s0 += MAX_SEG) {
-      cudaError_t e = engine_run(segs_dev + s0, std::min(MAX_SEG, nseg - s0), cfg, w, err, st);
-      if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-  }
   if (cfg.dom_block == 0 || cfg.dom_block > DBMAX) return cudaErrorInvalidValue;
+  if (w.task_cap > 0xffffffffull) return cudaErrorInvalidValue;
   Params P;
   P.segs = segs_dev;
   P.nseg = nseg;
   P.cfg = cfg;
   P.st = w.st;
-  P.done_round = w.done_round;
+  P.tbase = w.tbase;
   P.tdoneA = w.tdoneA;
   P.tdoneB = w.tdoneB;
   P.tcap = w.tcap;
+  P.tasks = reinterpret_cast<Task*>(w.tasks);
+  P.task_cap = (u32)w.task_cap;
   P.ctl = w.ctl;
   P.err = err;
-  size_t smem = 2 * (size_t)cfg.dom_block * sizeof(uint4) + 2 * (size_t)(nseg + 1) * sizeof(u32);
+  size_t smem = 2 * (size_t)cfg.dom_block * sizeof(uint4);
   cudaError_t e = cudaFuncSetAttribute(k_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -772,7 +820,10 @@ cudaError_t engine_run(const SegDesc* segs_dev, u32 nseg, const EngineCfg& cfg, 
   if (!g_sms) g_sms = device_sm_count();
   unsigned grid = (unsigned)(g_sms * per_sm);
   e = cudaMemsetAsync(w.ctl, 0, ENGINE_CTL_WORDS * sizeof(u32), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.tasks, 0, w.task_cap * sizeof(Task), st);
   if (e != cudaSuccess) return e;
+  // all CTAs co-resident: a CTA waiting for a ticket never holds up an SM
+  // that a CTA with work needs
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3(grid);
   lc.blockDim = dim3(THREADS);
@@ -789,5 +840,6 @@ cudaError_t engine_run(const SegDesc* segs_dev, u32 nseg, const EngineCfg& cfg, 
 
 u32 engine_max_round_word() { return C_MAXROUND; }
 u32 engine_max_dom_block() { return DBMAX; }
+size_t engine_task_bytes() { return sizeof(Task); }
 
 }  // namespace sky

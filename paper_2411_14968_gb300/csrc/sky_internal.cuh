@@ -194,7 +194,7 @@ struct SegDesc {
   u32 d;                 // attributes (1..8)
 };
 
-// Round state of a segment (two copies, alternating by round parity).
+// Round state of a segment (written by the CTA that starts the round).
 struct SegState {
   u32 cur;      // first position of the current chunk
   u32 cend;     // end of the current chunk (never splits a run of equal scores)
@@ -219,23 +219,28 @@ struct EngineCfg {
 };
 
 struct EngineWork {
-  SegState* st;       // 2 * nseg
-  u32* done_round;    // nseg
+  SegState* st;       // nseg
+  u32* tbase;         // nseg
   u32* tdoneA;        // engine_tile_capacity(...) counters, zero before the first launch
   u32* tdoneB;        // same
   u64 tcap;
+  void* tasks;        // engine_task_capacity(...) x engine_task_bytes() bytes
+  u64 task_cap;
   u32* ctl;           // ENGINE_CTL_WORDS control words
 };
 constexpr int ENGINE_CTL_WORDS = 16;
 u64 engine_tile_capacity(u64 total_points, u32 nseg);
+// Tasks (phases of segments) one launch can publish at most.
+u64 engine_task_capacity(u64 total_points, u32 nseg, u32 chunk_min);
+size_t engine_task_bytes();
 // Control word that receives the largest round count of a launch.
 u32 engine_max_round_word();
 // Largest dominator block (points) the engine stages in shared memory.
 u32 engine_max_dom_block();
 
-// Local skylines of segs[0..nseg) in one cooperative launch (grid = the
-// co-resident capacity).  Kills dominated points (alive = 0) and leaves each
-// segment's skyline in its window.
+// Local skylines of segs[0..nseg) in one persistent launch (grid = the
+// co-resident capacity) driven by a device-side work queue.  Kills dominated
+// points (alive = 0) and leaves each segment's skyline in its window.
 cudaError_t engine_run(const SegDesc* segs_dev, u32 nseg, const EngineCfg& cfg, const EngineWork& w, u32* err,
                        cudaStream_t st);
 

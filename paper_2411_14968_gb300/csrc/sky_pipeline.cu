@@ -102,10 +102,12 @@ struct BatchBufs {
   SegDesc* segs;    // local-phase segments of every query
   SegDesc* msegs;   // merge segments (one per query with a sequential final phase)
   SegState* st;
-  u32* done_round;
+  u32* tbase;
   u32* tdoneA;
   u32* tdoneB;
   u64 tcap;
+  void* tasks;
+  u64 task_cap;
   u32* ctl;
 };
 
@@ -167,15 +169,17 @@ size_t layout(const Plan& pl, u32 ang_words, Carve& c, Bufs* b) {
   return c.off - start;
 }
 
-void layout_batch(u64 total_pts, u32 total_segs, u32 nmerge, Carve& c, BatchBufs* bb) {
+void layout_batch(u64 total_pts, u32 total_segs, u32 nmerge, u32 chunk_min, Carve& c, BatchBufs* bb) {
   const u32 nseg = std::max(std::max(total_segs, nmerge), 1u);
   bb->segs = c.take<SegDesc>(std::max(total_segs, 1u));
   bb->msegs = c.take<SegDesc>(std::max(nmerge, 1u));
-  bb->st = c.take<SegState>(2 * (size_t)nseg);
-  bb->done_round = c.take<u32>(nseg);
+  bb->st = c.take<SegState>(nseg);
+  bb->tbase = c.take<u32>(nseg);
   bb->tcap = engine_tile_capacity(std::max<u64>(total_pts, 1), nseg);
   bb->tdoneA = c.take<u32>(bb->tcap);
   bb->tdoneB = c.take<u32>(bb->tcap);
+  bb->task_cap = engine_task_capacity(std::max<u64>(total_pts, 1), nseg, chunk_min);
+  bb->tasks = c.take<char>(bb->task_cap * engine_task_bytes());
   bb->ctl = c.take<u32>(ENGINE_CTL_WORDS);
 }
 
@@ -401,7 +405,7 @@ size_t Runner::query_bytes(u64 n, u32 d, const sky_params* params) {
   size_t q = layout(pl, (u32)std::max<size_t>(tab.size(), 1), c, &b);
   Carve c2(nullptr);
   BatchBufs bb;
-  layout_batch(n, pl.P, 1, c2, &bb);
+  layout_batch(n, pl.P, 1, pl.cfg.chunk_min, c2, &bb);
   return q + c2.off;
 }
 
@@ -412,7 +416,7 @@ sky_status Runner::run(Query* queries, u32 nq) {
   std::vector<Work> ws(nq);
   // ---- validate and size
   u64 total_pts = 0;
-  u32 total_segs = 0, nmerge = 0;
+  u32 total_segs = 0, nmerge = 0, min_chunk = 0xffffffffu;
   std::vector<size_t> offs(nq);
   size_t need = 0;
   for (u32 i = 0; i < nq; ++i) {
@@ -447,6 +451,7 @@ sky_status Runner::run(Query* queries, u32 nq) {
     need += layout(w.pl, (u32)std::max<size_t>(w.tab.size(), 1), c, &w.b);
     total_pts += q.n;
     total_segs += w.pl.P;
+    min_chunk = std::min(min_chunk, w.pl.cfg.chunk_min);
     if (w.pl.P > 1 && w.pl.merge == SKY_MERGE_SEQUENTIAL) ++nmerge;
   }
   for (u32 i = 0; i < nq; ++i)
@@ -455,7 +460,7 @@ sky_status Runner::run(Query* queries, u32 nq) {
   BatchBufs bb;
   {
     Carve c(nullptr, need);
-    layout_batch(total_pts, total_segs, nmerge, c, &bb);
+    layout_batch(total_pts, total_segs, nmerge, min_chunk, c, &bb);
     need = c.off;
   }
   sky_status s = ensure_ws(need);
@@ -472,7 +477,7 @@ sky_status Runner::run(Query* queries, u32 nq) {
       batch_off = std::max(batch_off, c.off);
     }
     Carve c(ws_, batch_off);
-    layout_batch(total_pts, total_segs, nmerge, c, &bb);
+    layout_batch(total_pts, total_segs, nmerge, min_chunk, c, &bb);
   }
   const cudaStream_t st = stream;
 
@@ -601,10 +606,12 @@ sky_status Runner::run(Query* queries, u32 nq) {
   // ---- ComputeLocalSet: u_i = Sky(r_i) for every partition of every query
   EngineWork ew;
   ew.st = bb.st;
-  ew.done_round = bb.done_round;
+  ew.tbase = bb.tbase;
   ew.tdoneA = bb.tdoneA;
   ew.tdoneB = bb.tdoneB;
   ew.tcap = bb.tcap;
+  ew.tasks = bb.tasks;
+  ew.task_cap = bb.task_cap;
   ew.ctl = bb.ctl;
   const u32* maxround = bb.ctl + engine_max_round_word();
   auto engine = [&](const SegDesc* segs, u32 nseg, const EngineCfg& cfg, u32* err, u32* round_dst) -> cudaError_t {
