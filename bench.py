@@ -273,16 +273,15 @@ def gpu_arm(args, rank, world, local):
     tuning = None
     knobs = {}
     if not args.no_autotune:
-        # the autotuner picks the engine knobs (SFS chunk sizes, dominator
-        # block) on the first variant; every variant and form then uses them
-        p0 = native.make_params(**VARIANTS[0][1])
-        default_ms = None
-        ctx.skyline(xt, params=p0)
-        ctx.skyline(xt, params=p0)
+        # the autotuner picks one set of engine knobs (SFS chunk sizes,
+        # dominator block) for the batched step as a whole
+        base = [(xt, native.make_params(**kw)) for _, kw in VARIANTS]
+        ctx.skyline_batch(base)
+        ctx.skyline_batch(base)
         default_ms = ctx.stats()["ms_total"]
-        tuned, best_ms = ctx.autotune(xt, p0, max_trials=40)
-        knobs = {k: getattr(tuned, k) for k in ("chunk_min", "chunk_max", "chunk_alpha_x4", "dom_block")}
-        tuning = {"tuned_on": VARIANTS[0][0], "knobs": knobs, "default_knobs_ms": default_ms, "tuned_ms": best_ms}
+        knobs, best_ms = ctx.autotune_batch(base, max_trials=40)
+        tuning = {"tuned_on": "the batched step", "knobs": knobs, "default_knobs_ms": default_ms,
+                  "tuned_ms": best_ms}
     persistent = {name: native.make_params(exec="persistent", **kw, **knobs) for name, kw in VARIANTS}
     plain = {name: native.make_params(exec="plain", **kw, **knobs) for name, kw in VARIANTS}
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -348,6 +347,26 @@ def gpu_arm(args, rank, world, local):
     total_s = max_over_ranks(sum(ms) / 1e3)
     pts_per_step = N * len(VARIANTS)
     value = throughput(pts_per_step * args.steps, world, total_s)
+
+    # the batched step captured into a CUDA graph and replayed
+    graph = None
+    if not args.no_graph:
+        step_batched()
+        batch_kernels = int(ctx.stats()["launches"])  # the graph holds the same kernels
+        g = ctx.capture([(xt, persistent[nm]) for nm in names])
+        for _ in range(max(args.warmup, 3)):
+            res, _ = g.run()
+            assert len({int(r.shape[0]) for r in res}) == 1
+        gms = []
+        for _ in range(args.steps):
+            flush.zero_()  # L2 flush between replays (before the replay's events)
+            _, m_ = g.run()
+            gms.append(m_)
+        g_s = max_over_ranks(sum(gms) / 1e3)
+        graph = {"value": throughput(pts_per_step * args.steps, world, g_s), "unit": "points/s",
+                 "ms_per_step": sum(gms) / len(gms), "kernels_per_replay": batch_kernels,
+                 "timing": "CUDA events around each replay on the graph's stream"}
+        g.close()
 
     # one query at a time, every partition of a query in one launch
     ms_pq, acc_pq = timed(lambda a: step_each(persistent, a), max(1, args.steps))
@@ -426,6 +445,7 @@ def gpu_arm(args, rank, world, local):
                                "all merges in a second",
                        "l2": "flushed between timed steps (256 MB write outside the timed events)",
                        "parallelism": f"replicas x{world}"},
+            "graph": graph,
             "per_query_persistent": {"value": pq_value, "unit": "points/s",
                                      "ms_per_step": sum(ms_pq) / len(ms_pq)},
             "plain": {"value": plain_value, "unit": "points/s", "ms_per_step": sum(ms_plain) / len(ms_plain),
@@ -472,6 +492,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run the small profiling case only: one query (anticorrelated N=200k, d=6, Sliced p=64) "
                          "twice, default knobs, no timing")

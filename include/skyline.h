@@ -182,6 +182,40 @@ sky_status sky_skyline_batch(sky_ctx* ctx, sky_query* queries, uint32_t nq);
 sky_status sky_autotune(sky_ctx* ctx, const float* points, uint64_t n, uint32_t d, sky_params* params,
                         uint32_t max_trials, double* best_ms);
 
+/* sky_autotune for a batch run by sky_skyline_batch: one set of knobs for
+   all queries (the queries share the engine's launches, so the best knobs
+   of a batch differ from those of its queries alone).  queries[i].params
+   hold the method parameters (their knobs are ignored); out_idx and
+   out_count of the queries are not used.  The four knob fields of *knobs
+   (struct_size set, e.g. by sky_params_init) receive the result. */
+sky_status sky_autotune_batch(sky_ctx* ctx, const sky_query* queries, uint32_t nq, uint32_t max_trials,
+                              sky_params* knobs, double* best_ms);
+
+/* ---- CUDA graphs ------------------------------------------------------
+   A batch (as sky_skyline_batch would run it) captured into a CUDA graph and
+   replayed with one graph launch: for a batch that is run again and again
+   over the same device buffers (inputs rewritten in place between runs),
+   the host's per-launch cost is paid once, at capture.  The graph owns its
+   own workspace, pinned staging and stream, so later calls on the context
+   cannot move its buffers.  Inputs and outputs must be device memory (the
+   per-point diagnostics are not captured); shapes, parameters and pointers
+   are fixed at capture.  Results equal sky_skyline_batch's. */
+typedef struct sky_graph sky_graph;
+
+/* Captures the batch (queries[i].out_count are ignored).  SKY_EINVAL for
+   invalid queries or host pointers; SKY_ECUDA if capture or instantiation
+   fails; *graph is NULL on failure.  The context's memory budget applies to
+   the graph's workspace. */
+sky_status sky_graph_capture(sky_ctx* ctx, const sky_query* queries, uint32_t nq, sky_graph** graph);
+
+/* Replays the graph after the work already queued on the context's stream
+   (at capture time) and waits for it.  out_counts (host, nq entries, may be
+   NULL) receive each query's |Sky|; *ms (may be NULL) the device time of
+   the replay.  Returns the first failing query's status. */
+sky_status sky_graph_launch(sky_graph* graph, uint64_t* out_counts, double* ms);
+
+void sky_graph_destroy(sky_graph* graph);
+
 /* ---- serving: a request loop with continuous batching ----------------
    sky_submit queues a query and returns at once.  Worker threads of the
    context take queued queries in arrival order into batches whose device

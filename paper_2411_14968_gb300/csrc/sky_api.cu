@@ -223,6 +223,58 @@ sky_status sky_serve_stop(sky_ctx* ctx) {
   return SKY_OK;
 }
 
+struct sky_graph {
+  GraphRun* run = nullptr;
+  cudaStream_t after = nullptr;
+  u32 nq = 0;
+  std::string error;
+};
+
+sky_status sky_graph_capture(sky_ctx* ctx, const sky_query* queries, uint32_t nq, sky_graph** graph) {
+  if (!graph) return SKY_EINVAL;
+  *graph = nullptr;
+  if (!ctx || (nq && !queries)) return SKY_EINVAL;
+  std::vector<Runner::Query> qs(nq);
+  std::vector<u64> dummy(nq);
+  for (u32 i = 0; i < nq; ++i) {
+    qs[i].points = queries[i].points;
+    qs[i].n = queries[i].n;
+    qs[i].d = queries[i].d;
+    qs[i].params = queries[i].params;
+    qs[i].out_idx = queries[i].out_idx;
+    qs[i].out_count = &dummy[i];
+  }
+  GraphRun* g = nullptr;
+  std::string msg;
+  sky_status s = graph_capture(ctx->run.device, ctx->run.budget, qs.data(), nq, &g, &msg);
+  if (s != SKY_OK) {
+    ctx->run.last_error = msg;
+    return s;
+  }
+  sky_graph* h = new sky_graph();
+  h->run = g;
+  h->after = ctx->run.stream;
+  h->nq = nq;
+  *graph = h;
+  return SKY_OK;
+}
+
+sky_status sky_graph_launch(sky_graph* graph, uint64_t* out_counts, double* ms) {
+  if (!graph) return SKY_EINVAL;
+  std::vector<sky_status> st(graph->nq);
+  std::vector<u64> counts(graph->nq);
+  sky_status s = graph_launch(graph->run, graph->after, counts.data(), st.data(), ms, nullptr, &graph->error);
+  if (out_counts)
+    for (u32 i = 0; i < graph->nq; ++i) out_counts[i] = counts[i];
+  return s;
+}
+
+void sky_graph_destroy(sky_graph* graph) {
+  if (!graph) return;
+  graph_destroy(graph->run);
+  delete graph;
+}
+
 sky_status sky_get_stats(sky_ctx* ctx, sky_stats* out) {
   if (!ctx || !out) return SKY_EINVAL;
   *out = ctx->run.stats;

@@ -20,10 +20,18 @@
 //      strongest, lowest-score skyline points); the survivors of each tile of
 //      the chunk are compacted into the segment's dense list;
 //   B. every dense-list point is tested against the rest of the window and
-//      against the whole dense list (a chunk dominator killed in phase A was
-//      itself dominated by a window point that also dominates the candidate,
-//      so the dense list holds every chunk dominator that matters); the
-//      survivors are appended to the window.
+//      against the dense-list points of lower or equal score (a chunk
+//      dominator killed in phase A was itself dominated by a window point
+//      that also dominates the candidate, so the dense list holds every chunk
+//      dominator that matters); the survivors are appended to the window.
+// In an ordered launch (the merge) the dense list is kept in position (=
+// score) order -- each tile writes its survivors at the sum of its
+// predecessors' counts, found by decoupled look-back -- so phase B tests a
+// dense tile only against the dense entries up to its end (extended over a
+// run of equal scores), half of the square.  The look-back makes a tile wait
+// for the scans of the tiles before it, which pays off for the merge's large
+// chunks but not for the local phase's many small segments, so local-phase
+// launches compact in arrival order and test the whole dense list.
 //
 // Work queue.  Segments advance through their rounds independently; there
 // is no grid-wide barrier.  A phase of a segment is a task of items (tile of
@@ -272,6 +280,7 @@ struct Params {
   u32* tbase;      // nseg: first completion counter of each segment
   u32* tdoneA;     // completion counters of phase-A tiles (capacity tcap)
   u32* tdoneB;     // completion counters of phase-B tiles (capacity tcap)
+  u32* tstat;      // phase-A tile status for the ordered compaction (capacity tcap)
   u64 tcap;
   Task* tasks;     // task_cap entries, valid flags zero before the launch
   u32 task_cap;
@@ -415,7 +424,14 @@ struct Shared {
   u32 bar_phase[2];
   u32 cursor;
   u32 flag;
+  u32 wtot[WARPS];
+  u32 tile_base;
 };
+
+// Tile status words of the ordered compaction (decoupled look-back): the
+// tile's survivor count, or the inclusive prefix of survivor counts up to
+// and including the tile.
+constexpr u32 TS_AGG = 1u << 30, TS_INC = 2u << 30, TS_VAL = TS_AGG - 1;
 
 // Producer (thread 0 only, never blocks): claims a ticket for buffer `slot`
 // if it has none, and once the ticket's task is known plans the item and
@@ -462,8 +478,19 @@ __device__ void produce(const Params& P, Shared& S, int slot, uint4* buf) {
       m.dense = 0;
       codes = sd->whc + m.base;
     } else {
+      // the dense list is in position (= score) order: a candidate of dense
+      // tile t can only be dominated by dense entries up to the end of the
+      // tile, extended over a run of scores equal to its last one
+      const u32 tend = P.cfg.ordered ? min(dlen, (m.tile + 1) * TILE) : dlen;
+      u32 e = tend;
+      if (tend < dlen) {
+        const float* sc = sd->score;
+        const float last = __ldg(sc + __ldcg(sd->dpos + tend - 1));
+        const float next = __ldg(sc + __ldcg(sd->dpos + tend));
+        if (next == last) e = dlen;  // a tie straddles the tile end (rare): all of the list
+      }
       m.base = (b - wbB) * DB;
-      m.cnt = min(DB, dlen - m.base);
+      m.cnt = m.base < e ? min(DB, e - m.base) : 0;
       m.dense = 1;
       codes = sd->dhc + m.base;
     }
@@ -529,20 +556,93 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
   __syncthreads();
   if (!S.flag) return;
   __threadfence();
-  // the tile's flags are final for phase A: compact its survivors
+  // The tile's flags are final for phase A: compact its survivors into the
+  // dense list in position order.  The tile's offset is the sum of its
+  // predecessors' survivor counts, found by decoupled look-back over the
+  // status words of the earlier tiles (all of which hold smaller tickets, so
+  // every one of them is being or has been processed).
+  if (!P.cfg.ordered) {
+    // unordered compaction: warp-level slots from one atomic per ballot
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      u32 pos = gbase + r * 32 + lane;
+      bool a = pos < cs.cend && ld_cg_u8(sd.alive + pos);
+      u32 m = __ballot_sync(FULL, a);
+      u32 base = 0;
+      if (lane == 0 && m) base = atomicAdd(&st->dlen, (u32)__popc(m));
+      base = __shfl_sync(FULL, base, 0);
+      if (a) {
+        u32 slot = base + __popc(m & ((1u << lane) - 1u));
+        sd.dpos[slot] = pos;
+        sd.dhc[slot] = __ldg(sd.hc + pos);
+      }
+    }
+  } else {
+  bool a[R];
+  u32 bal[R];
+  u32 wcount = 0;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     u32 pos = gbase + r * 32 + lane;
-    bool a = pos < cs.cend && ld_cg_u8(sd.alive + pos);
-    u32 m = __ballot_sync(FULL, a);
-    u32 base = 0;
-    if (lane == 0 && m) base = atomicAdd(&st->dlen, (u32)__popc(m));
-    base = __shfl_sync(FULL, base, 0);
-    if (a) {
-      u32 slot = base + __popc(m & ((1u << lane) - 1u));
-      sd.dpos[slot] = pos;
-      sd.dhc[slot] = __ldg(sd.hc + pos);
+    a[r] = pos < cs.cend && ld_cg_u8(sd.alive + pos);
+    bal[r] = __ballot_sync(FULL, a[r]);
+    wcount += __popc(bal[r]);
+  }
+  if (lane == 0) S.wtot[warp] = wcount;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u32 cnt_t = 0;
+    for (int w = 0; w < WARPS; ++w) cnt_t += S.wtot[w];
+    u32* stat = P.tstat + __ldcg(P.tbase + s);
+    u32 excl = 0;
+    if (mt.tile == 0) {
+      atomicExch(stat, TS_INC | cnt_t);
+    } else {
+      atomicExch(stat + mt.tile, TS_AGG | cnt_t);
+      u64 t0 = 0;
+      u32 seen = 0;
+      for (int j = (int)mt.tile - 1; j >= 0;) {
+        const u32 v = ld_vol_u32(stat + j);
+        if (v & TS_INC) {
+          excl += v & TS_VAL;
+          break;
+        }
+        if (v & TS_AGG) {
+          excl += v & TS_VAL;
+          --j;
+          continue;
+        }
+        // the predecessor has not counted its survivors yet: bounded wait
+        const u32 now = ld_vol_u32(P.ctl + C_PROGRESS);
+        if (t0 == 0 || now != seen) {
+          seen = now;
+          t0 = globaltimer();
+        } else if (globaltimer() - t0 > WAIT_NS || ld_vol_u32(P.ctl + C_ABORT)) {
+          abort_launch(P, ERR_TIMEOUT);
+          break;
+        }
+      }
+      atomicExch(stat + mt.tile, TS_INC | (excl + cnt_t));
     }
+    S.tile_base = excl;
+  }
+  __syncthreads();
+  {
+    u32 off = S.tile_base;
+    for (int w = 0; w < warp; ++w) off += S.wtot[w];
+    const u32 lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (a[r]) {
+        const u32 slot = off + __popc(bal[r] & lt);
+        const u32 pos = gbase + r * 32 + lane;
+        sd.dpos[slot] = pos;
+        sd.dhc[slot] = __ldg(sd.hc + pos);
+      }
+      off += __popc(bal[r]);
+    }
+    if (lane == 0 && wcount) atomicAdd(&st->dlen, wcount);
+  }
   }
   __threadfence();
   fence_proxy_async();
@@ -550,9 +650,14 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
   if (threadIdx.x == 0) {
     u32 old = atomicAdd(&st->done_a, 1u);
     if (old == cs.tiles - 1) {
-      // last tile of phase A: publish phase B, or the next round if nothing
-      // survived
+      // last tile of phase A: every tile has finished its look-back, so the
+      // status words are cleared for the next round; then publish phase B,
+      // or the next round if nothing survived
       __threadfence();
+      if (P.cfg.ordered) {
+        u32* stat = P.tstat + __ldcg(P.tbase + s);
+        for (u32 j = 0; j < cs.tiles; ++j) stat[j] = 0;
+      }
       const u32 dl = atomicAdd(&st->dlen, 0u);
       if (dl == 0) {
         SegState nx;
@@ -591,19 +696,21 @@ __device__ void item_b(const Params& P, const SegDesc& sd, const Meta& mt, const
   const u32 dbase = mt.tile * TILE + warp * GS;
   const u32 cnt = mt.cnt;
   const DomSrc src = mt.dense ? DomSrc{sd.pts, sd.dpos, mt.base} : DomSrc{sd.win, nullptr, mt.base};
-  Cands c;
+  if (cnt) {  // an item past the triangular bound has nothing to test
+    Cands c;
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    u32 e = dbase + r * 32 + lane;
-    bool valid = e < cs.dlen;
-    u32 pos = valid ? __ldcg(sd.dpos + e) : 0;
-    load_cand<D>(sd, pos, valid, c, r);
-  }
-  if (cnt && __any_sync(FULL, any_alive(c))) {
-    scan_smem<D>(staged, cnt, src, sd.pts, c);
+    for (int r = 0; r < R; ++r) {
+      u32 e = dbase + r * 32 + lane;
+      bool valid = e < cs.dlen;
+      u32 pos = valid ? __ldcg(sd.dpos + e) : 0;
+      load_cand<D>(sd, pos, valid, c, r);
+    }
+    if (__any_sync(FULL, any_alive(c))) {
+      scan_smem<D>(staged, cnt, src, sd.pts, c);
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-      if (c.was[r] && !c.alive[r]) sd.alive[c.pos[r]] = 0;
+      for (int r = 0; r < R; ++r)
+        if (c.was[r] && !c.alive[r]) sd.alive[c.pos[r]] = 0;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -805,6 +912,7 @@ cudaError_t engine_run(const SegDesc* segs_dev, u32 nseg, const EngineCfg& cfg, 
   P.tbase = w.tbase;
   P.tdoneA = w.tdoneA;
   P.tdoneB = w.tdoneB;
+  P.tstat = w.tstat;
   P.tcap = w.tcap;
   P.tasks = reinterpret_cast<Task*>(w.tasks);
   P.task_cap = (u32)w.task_cap;
@@ -821,21 +929,16 @@ cudaError_t engine_run(const SegDesc* segs_dev, u32 nseg, const EngineCfg& cfg, 
   unsigned grid = (unsigned)(g_sms * per_sm);
   e = cudaMemsetAsync(w.ctl, 0, ENGINE_CTL_WORDS * sizeof(u32), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.tasks, 0, w.task_cap * sizeof(Task), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w.tstat, 0, w.tcap * sizeof(u32), st);
   if (e != cudaSuccess) return e;
-  // all CTAs co-resident: a CTA waiting for a ticket never holds up an SM
-  // that a CTA with work needs
-  cudaLaunchConfig_t lc = {};
-  lc.gridDim = dim3(grid);
-  lc.blockDim = dim3(THREADS);
-  lc.dynamicSmemBytes = smem;
-  lc.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  lc.attrs = attr;
-  lc.numAttrs = 1;
+  // One CTA per resident slot.  No CTA ever waits for one that is not
+  // resident: a CTA waits only for work published by CTAs that hold
+  // earlier tickets (or, in the ordered compaction, for earlier tiles), and
+  // a CTA takes a ticket only once it runs, so the launch needs no
+  // co-residency guarantee (and can be captured into a CUDA graph).
   note_launch();
-  return cudaLaunchKernelEx(&lc, k_engine, P);
+  k_engine<<<grid, THREADS, smem, st>>>(P);
+  return cudaGetLastError();
 }
 
 u32 engine_max_round_word() { return C_MAXROUND; }

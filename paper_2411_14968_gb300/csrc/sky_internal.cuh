@@ -216,6 +216,10 @@ constexpr u32 DEFAULT_DOM_BLOCK = 1024;
 
 struct EngineCfg {
   u32 chunk_min, chunk_max, alpha_x4, dom_block;
+  // 1: keep each segment's dense list in position order (look-back between
+  // tiles) so phase B tests only the lower-score half of the dense square;
+  // pays off for large chunks (the merge), costs waits for many small ones
+  u32 ordered;
 };
 
 struct EngineWork {
@@ -223,6 +227,7 @@ struct EngineWork {
   u32* tbase;         // nseg
   u32* tdoneA;        // engine_tile_capacity(...) counters, zero before the first launch
   u32* tdoneB;        // same
+  u32* tstat;         // same count of tile status words
   u64 tcap;
   void* tasks;        // engine_task_capacity(...) x engine_task_bytes() bytes
   u64 task_cap;

@@ -13,11 +13,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include "sky_pipeline.cuh"
 
 namespace sky {
 
-namespace {
+namespace pipe {
 
 // Bump allocator over one scratch block; sizes are rounded to 256 bytes.
 struct Carve {
@@ -105,11 +106,16 @@ struct BatchBufs {
   u32* tbase;
   u32* tdoneA;
   u32* tdoneB;
+  u32* tstat;
   u64 tcap;
   void* tasks;
   u64 task_cap;
   u32* ctl;
 };
+
+// Local-phase launches with at most this many segments keep ordered dense
+// lists (large chunks); launches with more compact in arrival order.
+constexpr u32 ORDERED_MAX_SEGS = 8;
 
 // word slots of Bufs::words
 enum { W_ERR = 0, W_COLMAX = 1, W_GRID_DROPPED = 9, W_KEPT = 10, W_NU = 11, W_SKY = 12, W_MAXROUND_LOCAL = 13,
@@ -178,6 +184,7 @@ void layout_batch(u64 total_pts, u32 total_segs, u32 nmerge, u32 chunk_min, Carv
   bb->tcap = engine_tile_capacity(std::max<u64>(total_pts, 1), nseg);
   bb->tdoneA = c.take<u32>(bb->tcap);
   bb->tdoneB = c.take<u32>(bb->tcap);
+  bb->tstat = c.take<u32>(bb->tcap);
   bb->task_cap = engine_task_capacity(std::max<u64>(total_pts, 1), nseg, chunk_min);
   bb->tasks = c.take<char>(bb->task_cap * engine_task_bytes());
   bb->ctl = c.take<u32>(ENGINE_CTL_WORDS);
@@ -294,6 +301,9 @@ struct Work {
   int mseg = -1;             // merge segment, or -1
   bool out_dev = false;
   u32 words[W_WORDS] = {0};
+  size_t tab_off = 0;        // angular table in the pinned staging (words)
+  bool pid_dev = false;      // out_pid / out_stage are device memory
+  bool stage_dev = false;
 };
 
 #define CK(expr)                                                                       \
@@ -302,7 +312,22 @@ struct Work {
     if (e_ != cudaSuccess) return fail(SKY_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-}  // namespace
+}  // namespace pipe
+
+using namespace pipe;
+
+// Everything one batch keeps between its stages (prepare, enqueue, finish).
+struct BatchState {
+  Runner::Query* queries = nullptr;
+  u32 nq = 0;
+  std::vector<Work> ws;
+  BatchBufs bb{};
+  bool empty = false;
+  bool graph = false;         // captured into a CUDA graph: no host round trips
+  Work* first_persistent = nullptr;
+  u64 launches0 = 0;
+  u64 kernels = 0;            // kernel launches the device work issues
+};
 
 sky_status validate_query(const float* points, u64 n, u32 d, const sky_params* params, std::string* msg) {
   Plan pl;
@@ -388,10 +413,6 @@ sky_status Runner::ensure_pinned(size_t words) {
   return SKY_OK;
 }
 
-void Runner::record(int i) {
-  if (timing) cudaEventRecord(ev_[i], stream);
-}
-
 size_t Runner::query_bytes(u64 n, u32 d, const sky_params* params) {
   Plan pl;
   std::string msg;
@@ -410,10 +431,23 @@ size_t Runner::query_bytes(u64 n, u32 d, const sky_params* params) {
 }
 
 sky_status Runner::run(Query* queries, u32 nq) {
-  const u64 launches0 = launch_counter();
+  BatchState B;
+  sky_status s = prepare(B, queries, nq, false);
+  if (s != SKY_OK || B.empty) return s;
+  s = enqueue(B);
+  if (s != SKY_OK) return s;
+  return finish(B);
+}
+
+sky_status Runner::prepare(BatchState& B, Query* queries, u32 nq, bool graph) {
+  B.queries = queries;
+  B.nq = nq;
+  B.graph = graph;
+  B.launches0 = launch_counter();
   memset(&stats, 0, sizeof(stats));
   CK(cudaSetDevice(device));
-  std::vector<Work> ws(nq);
+  std::vector<Work>& ws = B.ws;
+  ws.assign(nq, Work());
   // ---- validate and size
   u64 total_pts = 0;
   u32 total_segs = 0, nmerge = 0, min_chunk = 0xffffffffu;
@@ -445,6 +479,13 @@ sky_status Runner::run(Query* queries, u32 nq) {
     if (q.n == 0) continue;
     w.pl.x_on_host = !is_device_ptr(q.points);
     w.out_dev = is_device_ptr(q.out_idx);
+    w.pid_dev = q.out_pid && is_device_ptr(q.out_pid);
+    w.stage_dev = q.out_stage && is_device_ptr(q.out_stage);
+    if (graph && (w.pl.x_on_host || !w.out_dev || (q.out_pid && !is_device_ptr(q.out_pid)) ||
+                  (q.out_stage && !is_device_ptr(q.out_stage)))) {
+      q.status = SKY_EINVAL;
+      return fail(SKY_EINVAL, "a captured batch needs device inputs and outputs");
+    }
     if (w.pl.scheme == SCHEME_ANGULAR) angular_table(w.pl, &w.tab, w.ang_off);
     Carve c(nullptr, need);
     offs[i] = need;
@@ -456,8 +497,11 @@ sky_status Runner::run(Query* queries, u32 nq) {
   }
   for (u32 i = 0; i < nq; ++i)
     if (queries[i].n == 0) *queries[i].out_count = 0;
-  if (total_pts == 0) return SKY_OK;
-  BatchBufs bb;
+  if (total_pts == 0) {
+    B.empty = true;
+    return SKY_OK;
+  }
+  BatchBufs& bb = B.bb;
   {
     Carve c(nullptr, need);
     layout_batch(total_pts, total_segs, nmerge, min_chunk, c, &bb);
@@ -465,8 +509,17 @@ sky_status Runner::run(Query* queries, u32 nq) {
   }
   sky_status s = ensure_ws(need);
   if (s != SKY_OK) return s;
-  s = ensure_pinned((size_t)nq * W_WORDS);
+  // pinned staging: the result words of every query, then the Angular
+  // threshold tables (copied to the device from here)
+  size_t pinned_words = (size_t)nq * W_WORDS;
+  for (auto& w : ws) {
+    w.tab_off = pinned_words;
+    pinned_words += w.tab.size();
+  }
+  s = ensure_pinned(pinned_words);
   if (s != SKY_OK) return s;
+  for (auto& w : ws)
+    if (!w.tab.empty()) memcpy(pinned_ + w.tab_off, w.tab.data(), w.tab.size() * sizeof(float));
   {
     size_t batch_off = 0;
     for (u32 i = 0; i < nq; ++i) {
@@ -479,8 +532,6 @@ sky_status Runner::run(Query* queries, u32 nq) {
     Carve c(ws_, batch_off);
     layout_batch(total_pts, total_segs, nmerge, min_chunk, c, &bb);
   }
-  const cudaStream_t st = stream;
-
   // Segment order: persistent queries first (one launch covers them), then
   // queries that ask for one launch per partition.
   {
@@ -494,7 +545,20 @@ sky_status Runner::run(Query* queries, u32 nq) {
       }
   }
 
-  record(0);
+  return SKY_OK;
+}
+
+void Runner::record(int i, const BatchState& B) {
+  if (timing && !B.graph) cudaEventRecord(ev_[i], stream);
+}
+
+sky_status Runner::enqueue(BatchState& B) {
+  std::vector<Work>& ws = B.ws;
+  BatchBufs& bb = B.bb;
+  const u32 nq = B.nq;
+  const cudaStream_t st = stream;
+  const u64 k0 = launch_counter();
+  record(0, B);
   for (auto& w : ws) {
     if (w.q->n == 0) continue;
     w.X = w.q->points;
@@ -503,7 +567,7 @@ sky_status Runner::run(Query* queries, u32 nq) {
       w.X = w.b.X;
     }
   }
-  record(1);
+  record(1, B);
 
   // ---- Partition(r, p): keys, sort, gather (Algorithm 2 first phase)
   for (auto& w : ws) {
@@ -525,7 +589,8 @@ sky_status Runner::run(Query* queries, u32 nq) {
     for (int a = 0; a < 8; ++a) pr.slices[a] = pl.slices[a];
     pr.colmax = b.words + W_COLMAX;
     if (pl.scheme == SCHEME_ANGULAR) {
-      CK(cudaMemcpyAsync(b.ang_table, w.tab.data(), w.tab.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(b.ang_table, pinned_ + w.tab_off, w.tab.size() * sizeof(float), cudaMemcpyHostToDevice,
+                         st));
       for (int a = 0; a < 8; ++a) pr.ang_off[a] = w.ang_off[a];
     }
     pr.ang_table = b.ang_table;
@@ -569,7 +634,7 @@ sky_status Runner::run(Query* queries, u32 nq) {
     ga.seg_off = b.seg_off;
     CK(launch_gather(ga, D, st));
   }
-  record(2);
+  record(2, B);
 
   // ---- Grid Filtering (3.2), Sorted representatives (4.1), segments
   for (auto& w : ws) {
@@ -601,7 +666,7 @@ sky_status Runner::run(Query* queries, u32 nq) {
     SegArrays sa{b.pts, b.hc, b.score, b.alive, b.win, b.whc, b.dpos, b.dhc};
     CK(launch_build_segs(b.seg_off, P, w.dropped, sa, D, bb.segs + w.seg_base, st));
   }
-  record(3);
+  record(3, B);
 
   // ---- ComputeLocalSet: u_i = Sky(r_i) for every partition of every query
   EngineWork ew;
@@ -609,12 +674,15 @@ sky_status Runner::run(Query* queries, u32 nq) {
   ew.tbase = bb.tbase;
   ew.tdoneA = bb.tdoneA;
   ew.tdoneB = bb.tdoneB;
+  ew.tstat = bb.tstat;
   ew.tcap = bb.tcap;
   ew.tasks = bb.tasks;
   ew.task_cap = bb.task_cap;
   ew.ctl = bb.ctl;
   const u32* maxround = bb.ctl + engine_max_round_word();
-  auto engine = [&](const SegDesc* segs, u32 nseg, const EngineCfg& cfg, u32* err, u32* round_dst) -> cudaError_t {
+  auto engine = [&](const SegDesc* segs, u32 nseg, EngineCfg cfg, u32* err, u32* round_dst,
+                    u32 ordered) -> cudaError_t {
+    cfg.ordered = ordered;
     cudaError_t e = cudaMemsetAsync(bb.tdoneA, 0, bb.tcap * sizeof(u32), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(bb.tdoneB, 0, bb.tcap * sizeof(u32), st);
     if (e != cudaSuccess) return e;
@@ -632,30 +700,32 @@ sky_status Runner::run(Query* queries, u32 nq) {
   };
   // the error word and round counter of a shared launch go to the first
   // query of the launch; the host folds them into every query of it
-  Work* first_persistent = nullptr;
+  Work*& first_persistent = B.first_persistent;
+  first_persistent = nullptr;
   u32 persistent_segs = 0;
   for (auto& w : ws) {
     if (w.q->n == 0 || w.pl.exec == SKY_EXEC_PLAIN) continue;
     if (!first_persistent) first_persistent = &w;
     persistent_segs += w.pl.P;
   }
-  record(8);
+  record(8, B);
   if (first_persistent) {
     // the engine's chunk policy of a shared launch is the first query's
+    // a local phase with few segments has large chunks, like the merge
     CK(engine(bb.segs, persistent_segs, first_persistent->pl.cfg, first_persistent->b.words + W_ERR,
-              first_persistent->b.words + W_MAXROUND_LOCAL));
+              first_persistent->b.words + W_MAXROUND_LOCAL, persistent_segs <= ORDERED_MAX_SEGS));
   }
   for (auto& w : ws) {
     if (w.q->n == 0 || w.pl.exec != SKY_EXEC_PLAIN) continue;
     for (u32 p = 0; p < w.pl.P; ++p)
-      CK(engine(bb.segs + w.seg_base + p, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_LOCAL));
+      CK(engine(bb.segs + w.seg_base + p, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_LOCAL, 1));
   }
-  record(9);
+  record(9, B);
   for (auto& w : ws) {
     if (w.q->n == 0) continue;
     CK(launch_stamp_stage(w.b.alive, w.pl.n, w.b.stage_s, ST_LOCAL, st));
   }
-  record(4);
+  record(4, B);
 
   // ---- final phase over u (sequential Sky(u), or NoSeq, Section 4.2)
   for (auto& w : ws) {
@@ -700,7 +770,7 @@ sky_status Runner::run(Query* queries, u32 nq) {
       CK(launch_scatter_alive(b.ualive, b.upos, n, nu_dev, b.alive, b.stage_s, ST_MERGE, st));
     }
   }
-  record(10);
+  record(10, B);
   {
     Work* first = nullptr;
     u32 cnt = 0;
@@ -709,18 +779,19 @@ sky_status Runner::run(Query* queries, u32 nq) {
         if (!first) first = &w;
         ++cnt;
       }
-    if (first) CK(engine(bb.msegs, cnt, first->pl.cfg, first->b.words + W_ERR, first->b.words + W_MAXROUND_MERGE));
+    if (first)
+      CK(engine(bb.msegs, cnt, first->pl.cfg, first->b.words + W_ERR, first->b.words + W_MAXROUND_MERGE, 1));
     for (auto& w : ws)
       if (w.mseg >= 0 && w.pl.exec == SKY_EXEC_PLAIN)
-        CK(engine(bb.msegs + w.mseg, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_MERGE));
+        CK(engine(bb.msegs + w.mseg, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_MERGE, 1));
   }
-  record(11);
+  record(11, B);
   for (auto& w : ws) {
     if (w.mseg < 0) continue;
     Bufs& b = w.b;
     CK(launch_scatter_alive(b.malive, b.mpos, w.pl.n, b.words + W_NU, b.alive, b.stage_s, ST_MERGE, st));
   }
-  record(5);
+  record(5, B);
 
   // ---- output: ascending indices of Sky(r)
   for (u32 i = 0; i < nq; ++i) {
@@ -730,22 +801,31 @@ sky_status Runner::run(Query* queries, u32 nq) {
     const u64 n = w.pl.n;
     u32* out_pid = w.q->out_pid;
     u8* out_stage = w.q->out_stage;
-    CK(launch_output(b.stage_s, b.orig, b.spid, n, b.mask,
-                     out_stage && is_device_ptr(out_stage) ? out_stage : nullptr,
-                     out_pid && is_device_ptr(out_pid) ? out_pid : nullptr, st));
+    CK(launch_output(b.stage_s, b.orig, b.spid, n, b.mask, w.stage_dev ? out_stage : nullptr,
+                     w.pid_dev ? out_pid : nullptr, st));
     CK(scan_u8(b.mask, b.excl, n, true, b.scan_tmp, st));
     CK(cudaMemcpyAsync(b.words + W_SKY, b.scan_tmp + scan_total_index(n), sizeof(u32), cudaMemcpyDeviceToDevice,
                        st));
     CK(launch_compact_idx(b.mask, b.excl, n, w.out_dev ? w.q->out_idx : b.out_dev, st));
     CK(launch_stage_hist(b.stage_s, n, b.words + W_HIST, st));
   }
-  record(6);
+  record(6, B);
   for (u32 i = 0; i < nq; ++i) {
     Work& w = ws[i];
     if (w.q->n == 0) continue;
     CK(cudaMemcpyAsync(pinned_ + (size_t)i * W_WORDS, w.b.words, W_WORDS * sizeof(u32), cudaMemcpyDeviceToHost,
                        st));
   }
+  B.kernels = launch_counter() - k0;
+  return SKY_OK;
+}
+
+sky_status Runner::finish(BatchState& B) {
+  std::vector<Work>& ws = B.ws;
+  const u32 nq = B.nq;
+  Query* queries = B.queries;
+  Work* first_persistent = B.first_persistent;
+  const cudaStream_t st = stream;
   CK(cudaStreamSynchronize(st));
   // the error word and round counts of a shared engine launch were written
   // to its first query: every query of the launch shares them
@@ -796,12 +876,11 @@ sky_status Runner::run(Query* queries, u32 nq) {
     const u64 n = w.pl.n;
     if (!w.out_dev && cnt) CK(cudaMemcpyAsync(q.out_idx, b.out_dev, cnt * sizeof(u32), cudaMemcpyDeviceToHost, st));
     // host-side diagnostics
-    if (q.out_stage && !is_device_ptr(q.out_stage)) {
+    if (q.out_stage && !w.stage_dev) {
       CK(launch_output(b.stage_s, b.orig, b.spid, n, b.mask, reinterpret_cast<u8*>(b.keys[0]), b.vals[0], st));
       CK(cudaMemcpyAsync(q.out_stage, b.keys[0], n, cudaMemcpyDeviceToHost, st));
-      if (q.out_pid && !is_device_ptr(q.out_pid))
-        CK(cudaMemcpyAsync(q.out_pid, b.vals[0], n * 4, cudaMemcpyDeviceToHost, st));
-    } else if (q.out_pid && !is_device_ptr(q.out_pid)) {
+      if (q.out_pid && !w.pid_dev) CK(cudaMemcpyAsync(q.out_pid, b.vals[0], n * 4, cudaMemcpyDeviceToHost, st));
+    } else if (q.out_pid && !w.pid_dev) {
       CK(launch_output(b.stage_s, b.orig, b.spid, n, b.mask, nullptr, b.vals[0], st));
       CK(cudaMemcpyAsync(q.out_pid, b.vals[0], n * 4, cudaMemcpyDeviceToHost, st));
     }
@@ -816,7 +895,7 @@ sky_status Runner::run(Query* queries, u32 nq) {
     S.local_union = (u64)w.words[W_HIST + ST_MERGE] + w.words[W_HIST + ST_SKY];
     S.skyline = cnt;
   }
-  record(7);
+  record(7, B);
   CK(cudaStreamSynchronize(st));
   // batch statistics: sums over the queries, maxima of the round counts
   for (u32 i = 0; i < nq; ++i) {
@@ -832,8 +911,8 @@ sky_status Runner::run(Query* queries, u32 nq) {
     stats.local_union += S.local_union;
     stats.skyline += S.skyline;
   }
-  stats.launches = launch_counter() - launches0;
-  if (timing) {
+  stats.launches = B.graph ? B.kernels : launch_counter() - B.launches0;
+  if (timing && !B.graph) {
     float ms = 0;
     cudaEventElapsedTime(&ms, ev_[0], ev_[7]);
     stats.ms_total = ms;
@@ -850,6 +929,107 @@ sky_status Runner::run(Query* queries, u32 nq) {
   }
   if (first_bad != SKY_OK) return fail(first_bad, first_msg);
   return SKY_OK;
+}
+
+// ---------------------------------------------------------------- CUDA graphs
+
+struct StreamHolder {
+  cudaStream_t s = nullptr;
+  ~StreamHolder() {
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
+struct GraphRun {
+  StreamHolder stream;  // destroyed after the Runner that uses it
+  Runner R;
+  BatchState B;
+  std::vector<Runner::Query> qs;
+  std::vector<u64> counts;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t dep = nullptr, e0 = nullptr, e1 = nullptr;
+  ~GraphRun() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (cudaEvent_t e : {dep, e0, e1})
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+sky_status graph_capture(int device, size_t budget, const Runner::Query* queries, u32 nq, GraphRun** out,
+                         std::string* msg) {
+  *out = nullptr;
+  std::unique_ptr<GraphRun> g(new GraphRun());
+  sky_status s = g->R.init(device, budget);
+  if (s != SKY_OK) return s;
+  if (cudaStreamCreateWithFlags(&g->stream.s, cudaStreamNonBlocking) != cudaSuccess) return SKY_ECUDA;
+  g->R.stream = g->stream.s;
+  for (cudaEvent_t* e : {&g->dep, &g->e0, &g->e1})
+    if (cudaEventCreate(e) != cudaSuccess) return SKY_ECUDA;
+  g->qs.assign(queries, queries + nq);
+  g->counts.assign(nq, 0);
+  for (u32 i = 0; i < nq; ++i) g->qs[i].out_count = &g->counts[i];
+  s = g->R.prepare(g->B, g->qs.data(), nq, true);
+  if (s != SKY_OK) {
+    *msg = g->R.last_error;
+    return s;
+  }
+  if (!g->B.empty) {
+    if (cudaStreamBeginCapture(g->stream.s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SKY_ECUDA;
+    s = g->R.enqueue(g->B);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(g->stream.s, &graph);
+    if (s != SKY_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      *msg = s != SKY_OK ? g->R.last_error : std::string("stream capture: ") + cudaGetErrorString(e);
+      return s != SKY_OK ? s : SKY_ECUDA;
+    }
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *msg = std::string("graph instantiation: ") + cudaGetErrorString(e);
+      return SKY_ECUDA;
+    }
+  }
+  *out = g.release();
+  return SKY_OK;
+}
+
+sky_status graph_launch(GraphRun* g, cudaStream_t after, u64* counts, sky_status* statuses, double* ms,
+                        sky_stats* stats, std::string* msg) {
+  if (cudaSetDevice(g->R.device) != cudaSuccess) return SKY_ECUDA;
+  sky_status s = SKY_OK;
+  if (g->exec) {
+    // the replay starts after the work already queued on the caller's stream
+    if (cudaEventRecord(g->dep, after) != cudaSuccess || cudaStreamWaitEvent(g->stream.s, g->dep, 0) != cudaSuccess ||
+        cudaEventRecord(g->e0, g->stream.s) != cudaSuccess || cudaGraphLaunch(g->exec, g->stream.s) != cudaSuccess ||
+        cudaEventRecord(g->e1, g->stream.s) != cudaSuccess) {
+      *msg = std::string("graph launch: ") + cudaGetErrorString(cudaGetLastError());
+      return SKY_ECUDA;
+    }
+    s = g->R.finish(g->B);
+    if (ms) {
+      float t = 0;
+      cudaEventElapsedTime(&t, g->e0, g->e1);
+      *ms = t;
+    }
+    if (s != SKY_OK) *msg = g->R.last_error;
+  } else if (ms) {
+    *ms = 0;
+  }
+  for (size_t i = 0; i < g->qs.size(); ++i) {
+    if (counts) counts[i] = g->counts[i];
+    if (statuses) statuses[i] = g->qs[i].status;
+  }
+  if (stats) *stats = g->R.stats;
+  return s;
+}
+
+void graph_destroy(GraphRun* g) {
+  if (!g) return;
+  cudaSetDevice(g->R.device);
+  delete g;
 }
 
 }  // namespace sky

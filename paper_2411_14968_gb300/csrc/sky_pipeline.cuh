@@ -22,6 +22,8 @@ struct EngineGate {
 // receives the reason of a failure.
 sky_status validate_query(const float* points, u64 n, u32 d, const sky_params* params, std::string* msg);
 
+struct BatchState;
+
 // Execution state that the pipeline needs: a device, a stream, a grow-only
 // device workspace, pinned host staging and timing events.  One Runner runs
 // one batch at a time.
@@ -63,6 +65,15 @@ class Runner {
   // status (queries[i].status says which).
   sky_status run(Query* queries, u32 nq);
 
+  // run() in three stages, so that the device work of a batch can be
+  // captured into a CUDA graph: prepare (validate, size, lay out the
+  // workspace; graph = device inputs and outputs only), enqueue (every
+  // launch and copy of the batch on `stream`, no host round trip), finish
+  // (wait, read the counts, copy host outputs, statistics).
+  sky_status prepare(BatchState& B, Query* queries, u32 nq, bool graph);
+  sky_status enqueue(BatchState& B);
+  sky_status finish(BatchState& B);
+
   // Workspace bytes a query of this shape needs (for admission control).
   static size_t query_bytes(u64 n, u32 d, const sky_params* params);
 
@@ -76,9 +87,21 @@ class Runner {
   sky_status ensure_ws(size_t bytes);
   sky_status ensure_pinned(size_t words);
   sky_status fail(sky_status s, const std::string& msg);
-  void record(int i);
+  void record(int i, const BatchState& B);
 };
 
 bool is_device_ptr(const void* p);
+
+// A batch captured into a CUDA graph with its own Runner (workspace, pinned
+// staging, stream), replayed as one graph launch.  Inputs and outputs must
+// be device memory; shapes, parameters and pointers are fixed at capture.
+struct GraphRun;
+sky_status graph_capture(int device, size_t budget, const Runner::Query* queries, u32 nq, GraphRun** out,
+                         std::string* msg);
+// Replays after the work queued on `after`, waits, and reports each query's
+// |Sky| and status, the device time of the replay and the statistics.
+sky_status graph_launch(GraphRun* g, cudaStream_t after, u64* counts, sky_status* statuses, double* ms,
+                        sky_stats* stats, std::string* msg);
+void graph_destroy(GraphRun* g);
 
 }  // namespace sky

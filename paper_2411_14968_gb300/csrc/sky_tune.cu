@@ -5,6 +5,10 @@
 // times whole queries (CUDA events around the call on the context's stream)
 // and keeps the fastest.
 //
+// A batch is tuned as a whole (one set of knobs for all of its queries): the
+// best knobs for a batch differ from those of its queries alone, because
+// the queries share the engine's launches.
+//
 // Search: from the built-in defaults, a joint search over the chunk growth
 // factor and the first chunk length (the two knobs that interact most),
 // then coordinate descent: for each knob in turn every candidate value is
@@ -31,27 +35,49 @@ struct Knob {
 
 }  // namespace
 
-extern "C" sky_status sky_autotune(sky_ctx* ctx, const float* points, uint64_t n, uint32_t d, sky_params* params,
-                                   uint32_t max_trials, double* best_ms) {
-  if (!ctx || !params || !best_ms || params->struct_size != sizeof(sky_params)) return SKY_EINVAL;
-  if (n == 0) {
+namespace {
+
+// Tunes the knobs of every query of a batch together.  queries[i].params
+// are the method parameters; the trial outputs go to one scratch buffer.
+sky_status tune(sky_ctx* ctx, const sky_query* queries, uint32_t nq, uint32_t max_trials, sky_params* knobs,
+                double* best_ms) {
+  uint64_t total = 0;
+  for (uint32_t i = 0; i < nq; ++i) total += queries[i].n;
+  if (total == 0) {
     *best_ms = 0;
     return SKY_OK;
   }
   if (max_trials == 0) max_trials = 48;
   uint32_t* out = nullptr;
-  if (cudaMalloc(&out, n * sizeof(uint32_t)) != cudaSuccess) {
+  if (cudaMalloc(&out, total * sizeof(uint32_t)) != cudaSuccess) {
     cudaGetLastError();
     return SKY_ENOMEM;
   }
+  std::vector<sky_params> ps(nq);
+  std::vector<sky_query> qs(queries, queries + nq);
+  std::vector<uint64_t> counts(nq);
+  {
+    uint64_t off = 0;
+    for (uint32_t i = 0; i < nq; ++i) {
+      if (queries[i].params) {
+        ps[i] = *queries[i].params;
+      } else {
+        sky_params_init(&ps[i]);
+      }
+      qs[i].params = &ps[i];
+      qs[i].out_idx = out + off;
+      qs[i].out_count = &counts[i];
+      off += queries[i].n;
+    }
+  }
   const int timing_was = sky::ctx_timing(ctx);
   sky_set_timing(ctx, 1);
-  sky_params cur = *params;
+  sky_params cur = *knobs;
   if (!cur.dom_block) cur.dom_block = sky::DEFAULT_DOM_BLOCK;
   if (!cur.chunk_min) cur.chunk_min = sky::DEFAULT_CHUNK_MIN;
   if (!cur.chunk_max) cur.chunk_max = sky::DEFAULT_CHUNK_MAX;
   if (!cur.chunk_alpha_x4) cur.chunk_alpha_x4 = sky::DEFAULT_ALPHA_X4;
-  const Knob knobs[] = {
+  const Knob knob_set[] = {
       {&sky_params::chunk_alpha_x4, {4, 8, 16, 32, 64}},
       {&sky_params::dom_block, {256, 512, 1024, 2048}},
       {&sky_params::chunk_min, {256, 1024, 4096, 16384}},
@@ -59,11 +85,16 @@ extern "C" sky_status sky_autotune(sky_ctx* ctx, const float* points, uint64_t n
   };
   uint32_t trials = 0;
   sky_status status = SKY_OK;
-  auto measure = [&](const sky_params& p, double* ms) -> sky_status {
+  auto measure = [&](const sky_params& k, double* ms) -> sky_status {
+    for (uint32_t i = 0; i < nq; ++i) {
+      ps[i].chunk_min = k.chunk_min;
+      ps[i].chunk_max = k.chunk_max;
+      ps[i].chunk_alpha_x4 = k.chunk_alpha_x4;
+      ps[i].dom_block = k.dom_block;
+    }
     double best = DBL_MAX;
     for (int rep = 0; rep < 2; ++rep) {
-      uint64_t cnt = 0;
-      sky_status s = sky_skyline(ctx, points, n, d, &p, out, &cnt);
+      sky_status s = sky_skyline_batch(ctx, qs.data(), nq);
       if (s != SKY_OK) return s;
       sky_stats st;
       sky_get_stats(ctx, &st);
@@ -84,6 +115,7 @@ extern "C" sky_status sky_autotune(sky_ctx* ctx, const float* points, uint64_t n
       sky_params cand = cur;
       cand.chunk_alpha_x4 = al;
       cand.chunk_min = cm;
+      if (cand.chunk_max < cand.chunk_min) continue;
       double ms = 0;
       status = measure(cand, &ms);
       if (status == SKY_OK && ms < cur_ms) {
@@ -93,7 +125,7 @@ extern "C" sky_status sky_autotune(sky_ctx* ctx, const float* points, uint64_t n
     }
   for (int sweep = 0; sweep < 2 && status == SKY_OK; ++sweep) {
     bool changed = false;
-    for (const Knob& k : knobs) {
+    for (const Knob& k : knob_set) {
       for (uint32_t v : k.values) {
         if (trials >= max_trials || status != SKY_OK) break;
         if (cur.*(k.field) == v) continue;
@@ -114,7 +146,32 @@ extern "C" sky_status sky_autotune(sky_ctx* ctx, const float* points, uint64_t n
   cudaFree(out);
   sky_set_timing(ctx, timing_was);
   if (status != SKY_OK) return status;
-  *params = cur;
+  knobs->chunk_min = cur.chunk_min;
+  knobs->chunk_max = cur.chunk_max;
+  knobs->chunk_alpha_x4 = cur.chunk_alpha_x4;
+  knobs->dom_block = cur.dom_block;
   *best_ms = cur_ms;
   return SKY_OK;
+}
+
+}  // namespace
+
+extern "C" sky_status sky_autotune(sky_ctx* ctx, const float* points, uint64_t n, uint32_t d, sky_params* params,
+                                   uint32_t max_trials, double* best_ms) {
+  if (!ctx || !params || !best_ms || params->struct_size != sizeof(sky_params)) return SKY_EINVAL;
+  sky_query q;
+  memset(&q, 0, sizeof(q));
+  q.points = points;
+  q.n = n;
+  q.d = d;
+  q.params = params;
+  return tune(ctx, &q, 1, max_trials, params, best_ms);
+}
+
+extern "C" sky_status sky_autotune_batch(sky_ctx* ctx, const sky_query* queries, uint32_t nq, uint32_t max_trials,
+                                         sky_params* knobs, double* best_ms) {
+  if (!ctx || !knobs || !best_ms || (nq && !queries) || knobs->struct_size != sizeof(sky_params)) return SKY_EINVAL;
+  for (uint32_t i = 0; i < nq; ++i)
+    if (queries[i].params && queries[i].params->struct_size != sizeof(sky_params)) return SKY_EINVAL;
+  return tune(ctx, queries, nq, max_trials, knobs, best_ms);
 }

@@ -104,7 +104,8 @@ class SkyStats(ctypes.Structure):
 EXPORTS = ["sky_params_init", "sky_create", "sky_set_stream", "sky_set_timing", "sky_skyline",
            "sky_skyline_ex", "sky_get_stats", "sky_status_str", "sky_last_error", "sky_destroy",
            "sky_probe_compare_rate", "sky_skyline_static", "sky_skyline_batch", "sky_serve_config_init", "sky_query_bytes",
-           "sky_serve_start", "sky_submit", "sky_poll", "sky_wait", "sky_serve_stop", "sky_autotune"]
+           "sky_serve_start", "sky_submit", "sky_poll", "sky_wait", "sky_serve_stop", "sky_autotune", "sky_autotune_batch",
+           "sky_graph_capture", "sky_graph_launch", "sky_graph_destroy"]
 
 _lock = threading.Lock()
 _lib = None
@@ -161,6 +162,15 @@ def load(build_if_missing: bool = True):
         L.sky_query_bytes.restype = u64
         L.sky_autotune.argtypes = [P, P, u64, u32, ctypes.POINTER(SkyParams), u32, ctypes.POINTER(ctypes.c_double)]
         L.sky_autotune.restype = i32
+        L.sky_autotune_batch.argtypes = [P, ctypes.POINTER(SkyQuery), u32, u32, ctypes.POINTER(SkyParams),
+                                         ctypes.POINTER(ctypes.c_double)]
+        L.sky_autotune_batch.restype = i32
+        L.sky_graph_capture.argtypes = [P, ctypes.POINTER(SkyQuery), u32, ctypes.POINTER(P)]
+        L.sky_graph_capture.restype = i32
+        L.sky_graph_launch.argtypes = [P, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_double)]
+        L.sky_graph_launch.restype = i32
+        L.sky_graph_destroy.argtypes = [P]
+        L.sky_graph_destroy.restype = None
         L.sky_serve_start.argtypes = [P, ctypes.POINTER(SkyServeConfig)]
         L.sky_serve_start.restype = i32
         L.sky_submit.argtypes = [P, P, u64, u32, ctypes.POINTER(SkyParams), ctypes.POINTER(u64)]
@@ -332,6 +342,66 @@ class Context:
                                          int(max_trials), ctypes.byref(ms)))
         return params, ms.value
 
+    def autotune_batch(self, queries, max_trials: int = 0):
+        """Tunes one set of engine knobs for a batch (sky_autotune_batch).
+        queries: list of (points, params).  Returns (dict of the four knobs,
+        best batch time in ms)."""
+        nq = len(queries)
+        arr = (SkyQuery * max(nq, 1))()
+        keep = []
+        stream_set = False
+        for i, (pts, params) in enumerate(queries):
+            if params is None:
+                params = make_params()
+            if _is_cuda_tensor(pts):
+                import torch
+                pts = pts.contiguous()
+                if not stream_set:
+                    self.set_stream(torch.cuda.current_stream(pts.device).cuda_stream)
+                    stream_set = True
+                arr[i].points = pts.data_ptr()
+            else:
+                pts = np.ascontiguousarray(pts, dtype=np.float32)
+                arr[i].points = pts.ctypes.data
+            arr[i].n, arr[i].d = pts.shape
+            arr[i].params = ctypes.pointer(params)
+            keep.append((pts, params))
+        if not stream_set:
+            self.set_stream(0)
+        knobs = make_params()
+        ms = ctypes.c_double(0)
+        self._check(self._L.sky_autotune_batch(self._h, arr, nq, int(max_trials), ctypes.byref(knobs),
+                                               ctypes.byref(ms)))
+        return ({k: getattr(knobs, k) for k in ("chunk_min", "chunk_max", "chunk_alpha_x4", "dom_block")},
+                ms.value)
+
+    def capture(self, queries):
+        """Captures a batch of device-resident queries into a CUDA graph
+        (sky_graph_capture).  queries: list of (CUDA float32 [N, d] tensor,
+        params).  Returns a Graph whose run() replays it."""
+        import torch
+        nq = len(queries)
+        arr = (SkyQuery * max(nq, 1))()
+        keep, outs = [], []
+        for i, (pts, params) in enumerate(queries):
+            if params is None:
+                params = make_params()
+            if not _is_cuda_tensor(pts):
+                raise ValueError("a captured batch needs CUDA tensors")
+            pts = pts.contiguous()
+            n, d = pts.shape
+            out = torch.empty(max(n, 1), dtype=torch.int32, device=pts.device)
+            arr[i].points, arr[i].out_idx = pts.data_ptr(), out.data_ptr()
+            arr[i].n, arr[i].d = n, d
+            arr[i].params = ctypes.pointer(params)
+            keep.append((pts, params))
+            outs.append(out)
+        if nq:
+            self.set_stream(torch.cuda.current_stream(queries[0][0].device).cuda_stream)
+        h = ctypes.c_void_p()
+        self._check(self._L.sky_graph_capture(self._h, arr, nq, ctypes.byref(h)))
+        return Graph(self._L, h, keep, outs)
+
     # ---- serving (continuous batching) --------------------------------
     def serve_start(self, workers: int = 2, max_batch: int = 64, mem_budget_bytes: int = 0):
         cfg = SkyServeConfig()
@@ -434,6 +504,34 @@ class Context:
 def query_bytes(n: int, d: int, params: SkyParams | None = None) -> int:
     """Device memory one query of this shape takes in a batch (bytes)."""
     return int(load().sky_query_bytes(int(n), int(d), ctypes.byref(params) if params is not None else None))
+
+
+class Graph:
+    """A captured batch (sky_graph_*); keeps its inputs and outputs alive."""
+
+    def __init__(self, L, h, keep, outs):
+        self._L, self._h, self._keep, self.outs = L, h, keep, outs
+
+    def run(self):
+        """Replays the graph; returns (list of CUDA int32 index tensors, device ms)."""
+        n = len(self.outs)
+        counts = (ctypes.c_uint64 * max(n, 1))()
+        ms = ctypes.c_double(0)
+        st = self._L.sky_graph_launch(self._h, counts, ctypes.byref(ms))
+        if st != SKY_OK:
+            raise SkylineError(st, self._L.sky_status_str(st).decode())
+        return [o[: counts[i]] for i, o in enumerate(self.outs)], ms.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.sky_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 STATIC_MAX_POINTS = 65536

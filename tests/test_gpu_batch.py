@@ -92,3 +92,42 @@ def test_autotune_keeps_result_and_improves_or_keeps_time(ctx):
     assert tuned.scheme == base.scheme and tuned.num_partitions == 8 and tuned.rep == base.rep
     assert tuned.dom_block % 32 == 0 and tuned.chunk_max >= tuned.chunk_min > 0
     np.testing.assert_array_equal(ctx.skyline(x, params=tuned), want)
+
+
+def test_autotune_batch_keeps_results(ctx):
+    from paper_2411_14968_gb300 import native
+    xs = [datagen.anticorrelated(40000, 6, 61), datagen.anticorrelated(25000, 5, 62)]
+    ps = [native.make_params(scheme="sliced", p=8), native.make_params(scheme="angular", slices=[2, 2, 2, 2])]
+    want = [ctx.skyline(x, params=p) for x, p in zip(xs, ps)]
+    knobs, ms = ctx.autotune_batch(list(zip(xs, ps)), max_trials=10)
+    assert ms > 0 and knobs["dom_block"] % 32 == 0 and knobs["chunk_max"] >= knobs["chunk_min"] > 0
+    tuned = [native.make_params(scheme="sliced", p=8, **knobs),
+             native.make_params(scheme="angular", slices=[2, 2, 2, 2], **knobs)]
+    for g, w in zip(ctx.skyline_batch(list(zip(xs, tuned))), want):
+        np.testing.assert_array_equal(g, w)
+
+
+def test_graph_replay_matches_and_reads_inputs_at_replay(ctx):
+    import torch
+    from paper_2411_14968_gb300 import native
+    x0 = [datagen.anticorrelated(40000, 6, 71), datagen.independent(20000, 4, 72)]
+    x1 = [datagen.anticorrelated(40000, 6, 73), datagen.independent(20000, 4, 74)]
+    ps = [native.make_params(scheme="sliced", p=8, rep="sorted"), native.make_params(scheme="grid", slices=[3] * 4)]
+    want0 = [ctx.skyline(x, params=p) for x, p in zip(x0, ps)]
+    want1 = [ctx.skyline(x, params=p) for x, p in zip(x1, ps)]
+    xt = [torch.from_numpy(x).cuda() for x in x0]
+    g = ctx.capture(list(zip(xt, ps)))
+    for _ in range(2):
+        res, ms = g.run()
+        assert ms > 0
+        for r, w in zip(res, want0):
+            np.testing.assert_array_equal(r.cpu().numpy().astype(np.uint32), w)
+    # inputs rewritten in place: the replay reads them when it runs
+    for t, x in zip(xt, x1):
+        t.copy_(torch.from_numpy(x))
+    res, _ = g.run()
+    for r, w in zip(res, want1):
+        np.testing.assert_array_equal(r.cpu().numpy().astype(np.uint32), w)
+    g.close()
+    with pytest.raises(ValueError):
+        ctx.capture([(x0[0], ps[0])])
