@@ -468,19 +468,25 @@ def gpu_arm(args, rank, world, local):
         dist.destroy_process_group()
 
 
-def ncu_case():
-    """The small case the engine's ncu capture runs: its two k_engine launches
-    of the second call (local phase, merge) are the captured ones."""
+def ncu_case(which: str):
+    """The cases the engine's ncu captures run: the two k_engine launches
+    (local phase, merge) of the second call are the captured ones."""
     import torch
     from paper_2411_14968_gb300 import datagen, native
-    x = datagen.anticorrelated(200_000, 6, SEED)
+    n = 200_000 if which == "small" else N
+    x = datagen.anticorrelated(n, D, SEED)
     xt = torch.from_numpy(x).cuda()
     with native.Context(0) as ctx:
-        p = native.make_params(scheme="sliced", p=64)
-        for _ in range(2):
-            r = ctx.skyline(xt, params=p)
+        if which == "small":
+            p = native.make_params(scheme="sliced", p=64)
+            for _ in range(2):
+                r = ctx.skyline(xt, params=p)
+        else:
+            ps = [native.make_params(**kw) for _, kw in VARIANTS]
+            for _ in range(2):
+                r = ctx.skyline_batch([(xt, p) for p in ps])[0]
         torch.cuda.synchronize()
-        print(f"ncu case: |Sky| = {r.shape[0]}, {ctx.stats()['launches']} launches per call")
+        print(f"ncu case {which}: |Sky| = {r.shape[0]}, {ctx.stats()['launches']} launches per call")
 
 
 def main():
@@ -493,16 +499,16 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--ncu-case", action="store_true",
-                    help="run the small profiling case only: one query (anticorrelated N=200k, d=6, Sliced p=64) "
-                         "twice, default knobs, no timing")
+    ap.add_argument("--ncu-case", choices=["small", "batch"], default=None,
+                    help="run a profiling case only, twice, default knobs, no timing: 'small' = one query "
+                         "(anticorrelated N=200k, d=6, Sliced p=64); 'batch' = the benchmark's batched step")
     # FP32 compare peak: 152 SMs x 64 compare lanes per SM per clock x 2.07 GHz
     # (the compare-rate probe of the library measures 58.6 per SM per clock)
     ap.add_argument("--compare-peak-tcmp", type=float, default=SM_COUNT * 64 * 2.07e9 / 1e12)
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.ncu_case:
-        ncu_case()
+        ncu_case(args.ncu_case)
         return
     if args.impl == "reference":
         reference_arm(args, rank, world)
