@@ -177,6 +177,7 @@ __device__ __forceinline__ bool dominates_fp32(const float4* w, const float4* t)
   return le && ne;
 }
 
+constexpr int SCAN_U = 4;               // dominators per step of the scan loop
 constexpr u32 NEG_INF2 = 0xFC00FC00u;  // (-inf, -inf)
 constexpr u32 POS_INF2 = 0x7C007C00u;  // (+inf, +inf)
 
@@ -209,11 +210,13 @@ template <int D>
 __device__ __forceinline__ void scan_smem(const uint4* sb, u32 cnt, const DomSrc& src, const float4* pts,
                                           Cands& c) {
   constexpr int V = vec_of(D);
-  constexpr int U = 4;
+  constexpr int U = SCAN_U;
+  // the staged block is padded with +inf images up to a multiple of U, so
+  // the common path needs no bounds check (the rare FP32 path keeps one)
   for (u32 j = 0; j < cnt; j += U) {
     uint4 w[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) w[u] = (j + u < cnt) ? sb[j + u] : make_uint4(POS_INF2, POS_INF2, POS_INF2, POS_INF2);
+    for (int u = 0; u < U; ++u) w[u] = sb[j + u];
     bool hit = false;
 #pragma unroll
     for (int u = 0; u < U; ++u)
@@ -501,6 +504,10 @@ __device__ void produce(const Params& P, Shared& S, int slot, uint4* buf) {
     mbar_expect_tx(&S.bar[slot], m.cnt * 16u);
     bulk_g2s(buf, codes, m.cnt * 16u, &S.bar[slot]);
     m.copied = 1;
+    // +inf padding up to a multiple of the scan step (beyond the copied
+    // range, so it does not race with the copy); read after the CTA barrier
+    // that follows the copy's completion
+    for (u32 i = m.cnt; i % SCAN_U; ++i) buf[i] = make_uint4(POS_INF2, POS_INF2, POS_INF2, POS_INF2);
   }
   m.state = M_READY;
 }
@@ -815,7 +822,8 @@ __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
   extern __shared__ __align__(128) unsigned char dyn[];
   __shared__ Shared S;
   const u32 DB = P.cfg.dom_block;
-  uint4* const buf0 = reinterpret_cast<uint4*>(dyn);  // two buffers of DB FP16 images
+  uint4* const buf0 = reinterpret_cast<uint4*>(dyn);  // two buffers of DB (+ padding) FP16 images
+  const u32 BUFN = DB + SCAN_U;
 
   if (threadIdx.x == 0) {
     mbar_init(&S.bar[0]);
@@ -831,7 +839,7 @@ __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
   if (threadIdx.x == 0) produce(P, S, 0, buf0);
   for (u32 k = 0;; ++k) {
     const int slot = k & 1;
-    uint4* const cur_buf = buf0 + (size_t)slot * DB;
+    uint4* const cur_buf = buf0 + (size_t)slot * BUFN;
     // wait until the slot's ticket has a task (or there is no more work)
     if (threadIdx.x == 0) {
       u64 t0 = 0;
@@ -863,7 +871,7 @@ __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
     if (threadIdx.x == 0) {
       if (m.copied) S.bar_phase[slot] ^= 1u;
       S.meta[slot].state = M_EMPTY;
-      produce(P, S, slot ^ 1, buf0 + (size_t)(slot ^ 1) * DB);
+      produce(P, S, slot ^ 1, buf0 + (size_t)(slot ^ 1) * BUFN);
     }
     const SegDesc sd = P.segs[m.s];
     switch (sd.d) {
@@ -918,7 +926,7 @@ cudaError_t engine_run(const SegDesc* segs_dev, u32 nseg, const EngineCfg& cfg, 
   P.task_cap = (u32)w.task_cap;
   P.ctl = w.ctl;
   P.err = err;
-  size_t smem = 2 * (size_t)cfg.dom_block * sizeof(uint4);
+  size_t smem = 2 * ((size_t)cfg.dom_block + SCAN_U) * sizeof(uint4);
   cudaError_t e = cudaFuncSetAttribute(k_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
