@@ -23,9 +23,6 @@ constexpr int R = 2;             // candidates per lane
 constexpr int GS = 32 * R;       // candidates per group
 constexpr int IB = 4;            // items taken per atomic fetch
 
-// control word of the NoSeq work counter (the engine uses words 0..7)
-constexpr int C_NOSEQ_ITEMS = 12;
-
 __device__ __forceinline__ u8 ld_cg_u8(const u8* p) {
   return (u8)__ldcg(reinterpret_cast<const unsigned char*>(p));
 }
@@ -191,7 +188,7 @@ __device__ __forceinline__ bool in_pd(const NoSeqArgs& a, u32 i, u32 j) {
 // group counts per partition (computed on the device).
 template <int D>
 __global__ void __launch_bounds__(THREADS) k_noseq(NoSeqArgs a, const u32* __restrict__ gpre, const u32* nu_dev,
-                                                   u32* ctl) {
+                                                   u32* counter) {
   constexpr int V = vec_of(D);
   const int lane = threadIdx.x & 31;
   const u32 nu = *nu_dev;
@@ -201,7 +198,7 @@ __global__ void __launch_bounds__(THREADS) k_noseq(NoSeqArgs a, const u32* __res
   const u64 total = (u64)ngroups * nblocks;
   for (;;) {
     u32 first = 0;
-    if (lane == 0) first = atomicAdd(ctl + C_NOSEQ_ITEMS, (u32)IB);
+    if (lane == 0) first = atomicAdd(counter, (u32)IB);
     first = __shfl_sync(FULL, first, 0);
     if (first >= total) break;
     u64 lim = (u64)first + IB < total ? (u64)first + IB : total;
@@ -356,7 +353,7 @@ cudaError_t launch_relative(const float* cand, u8* alive, u64 nc, const float* d
   });
 }
 
-cudaError_t launch_noseq(const NoSeqArgs& a, u32* gcnt, u32* gpre, u32* scan_tmp, const u32* nu_dev, u32* ctl,
+cudaError_t launch_noseq(const NoSeqArgs& a, u32* gcnt, u32* gpre, u32* scan_tmp, const u32* nu_dev, u32* counter,
                          cudaStream_t st) {
   if (a.P == 0) return cudaSuccess;
   note_launch();
@@ -366,7 +363,7 @@ cudaError_t launch_noseq(const NoSeqArgs& a, u32* gcnt, u32* gpre, u32* scan_tmp
   // gpre[P] = total groups
   e = cudaMemcpyAsync(gpre + a.P, scan_tmp + scan_total_index(a.P), sizeof(u32), cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(ctl + C_NOSEQ_ITEMS, 0, sizeof(u32), st);
+  e = cudaMemsetAsync(counter, 0, sizeof(u32), st);
   if (e != cudaSuccess) return e;
   int sms = g_sm_count ? g_sm_count : device_sm_count();
   return dispatch_d(a.d, [&](auto D) {
@@ -374,7 +371,7 @@ cudaError_t launch_noseq(const NoSeqArgs& a, u32* gcnt, u32* gpre, u32* scan_tmp
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_noseq<decltype(D)::value>, THREADS, 0);
     if (per_sm <= 0) per_sm = 1;
     note_launch();
-    k_noseq<decltype(D)::value><<<(unsigned)(sms * per_sm), THREADS, 0, st>>>(a, gpre, nu_dev, ctl);
+    k_noseq<decltype(D)::value><<<(unsigned)(sms * per_sm), THREADS, 0, st>>>(a, gpre, nu_dev, counter);
   });
 }
 

@@ -284,7 +284,8 @@ struct NoSeqArgs {
   GridDims gd;       // Grid: slices per attribute
   u32 dom_block;
 };
-cudaError_t launch_noseq(const NoSeqArgs& a, u32* gcnt, u32* gpre, u32* scan_tmp, const u32* nu_dev, u32* ctl,
+// counter: one device word, the kernel's work counter (zeroed here).
+cudaError_t launch_noseq(const NoSeqArgs& a, u32* gcnt, u32* gpre, u32* scan_tmp, const u32* nu_dev, u32* counter,
                          cudaStream_t st);
 
 int device_sm_count();

@@ -119,7 +119,7 @@ constexpr u32 ORDERED_MAX_SEGS = 8;
 
 // word slots of Bufs::words
 enum { W_ERR = 0, W_COLMAX = 1, W_GRID_DROPPED = 9, W_KEPT = 10, W_NU = 11, W_SKY = 12, W_MAXROUND_LOCAL = 13,
-       W_MAXROUND_MERGE = 14, W_HIST = 16, W_WORDS = 32 };
+       W_MAXROUND_MERGE = 14, W_HIST = 16, W_NOSEQ_CTR = 24, W_WORDS = 32 };
 
 size_t layout(const Plan& pl, u32 ang_words, Carve& c, Bufs* b) {
   const size_t start = c.off;
@@ -353,6 +353,14 @@ Runner::~Runner() {
   for (auto& e : ev_)
     if (e) cudaEventDestroy(e);
   if (gate_ev_) cudaEventDestroy(gate_ev_);
+  if (fork_ev_) cudaEventDestroy(fork_ev_);
+  for (int k = 0; k < NAUX; ++k) {
+    if (aux_[k]) {
+      cudaStreamSynchronize(aux_[k]);
+      cudaStreamDestroy(aux_[k]);
+    }
+    if (join_ev_[k]) cudaEventDestroy(join_ev_[k]);
+  }
 }
 
 sky_status Runner::init(int dev, size_t mem_budget) {
@@ -362,6 +370,11 @@ sky_status Runner::init(int dev, size_t mem_budget) {
   for (auto& e : ev_)
     if (cudaEventCreate(&e) != cudaSuccess) return SKY_ECUDA;
   if (cudaEventCreateWithFlags(&gate_ev_, cudaEventDisableTiming) != cudaSuccess) return SKY_ECUDA;
+  if (cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming) != cudaSuccess) return SKY_ECUDA;
+  for (int k = 0; k < NAUX; ++k) {
+    if (cudaStreamCreateWithFlags(&aux_[k], cudaStreamNonBlocking) != cudaSuccess) return SKY_ECUDA;
+    if (cudaEventCreateWithFlags(&join_ev_[k], cudaEventDisableTiming) != cudaSuccess) return SKY_ECUDA;
+  }
   return ensure_pinned(64);
 }
 
@@ -558,20 +571,45 @@ sky_status Runner::enqueue(BatchState& B) {
   const u32 nq = B.nq;
   const cudaStream_t st = stream;
   const u64 k0 = launch_counter();
+  // Per-query work runs on up to NAUX streams forked from `st` (the small
+  // kernels of different queries overlap); the engine launches, which cover
+  // every query, run on `st` between the joins.
+  const bool multi = nq > 1;
+  auto fork = [&]() -> cudaError_t {
+    if (!multi) return cudaSuccess;
+    cudaError_t r = cudaEventRecord(fork_ev_, st);
+    for (int k = 0; k < NAUX && r == cudaSuccess; ++k) r = cudaStreamWaitEvent(aux_[k], fork_ev_, 0);
+    return r;
+  };
+  auto join = [&]() -> cudaError_t {
+    if (!multi) return cudaSuccess;
+    cudaError_t r = cudaSuccess;
+    for (int k = 0; k < NAUX && r == cudaSuccess; ++k) {
+      r = cudaEventRecord(join_ev_[k], aux_[k]);
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(st, join_ev_[k], 0);
+    }
+    return r;
+  };
+  auto qstream = [&](const Work& w) -> cudaStream_t { return multi ? aux_[(&w - ws.data()) % NAUX] : stream; };
   record(0, B);
+  CK(fork());
   for (auto& w : ws) {
     if (w.q->n == 0) continue;
+    const cudaStream_t st = qstream(w);
     w.X = w.q->points;
     if (w.pl.x_on_host) {
       CK(cudaMemcpyAsync(w.b.X, w.q->points, w.q->n * w.q->d * sizeof(float), cudaMemcpyHostToDevice, st));
       w.X = w.b.X;
     }
   }
+  CK(join());
   record(1, B);
 
   // ---- Partition(r, p): keys, sort, gather (Algorithm 2 first phase)
+  CK(fork());
   for (auto& w : ws) {
     if (w.q->n == 0) continue;
+    const cudaStream_t st = qstream(w);
     const Plan& pl = w.pl;
     Bufs& b = w.b;
     const u64 n = pl.n;
@@ -634,11 +672,14 @@ sky_status Runner::enqueue(BatchState& B) {
     ga.seg_off = b.seg_off;
     CK(launch_gather(ga, D, st));
   }
+  CK(join());
   record(2, B);
 
   // ---- Grid Filtering (3.2), Sorted representatives (4.1), segments
+  CK(fork());
   for (auto& w : ws) {
     if (w.q->n == 0) continue;
+    const cudaStream_t st = qstream(w);
     const Plan& pl = w.pl;
     Bufs& b = w.b;
     const u64 n = pl.n;
@@ -666,6 +707,7 @@ sky_status Runner::enqueue(BatchState& B) {
     SegArrays sa{b.pts, b.hc, b.score, b.alive, b.win, b.whc, b.dpos, b.dhc};
     CK(launch_build_segs(b.seg_off, P, w.dropped, sa, D, bb.segs + w.seg_base, st));
   }
+  CK(join());
   record(3, B);
 
   // ---- ComputeLocalSet: u_i = Sky(r_i) for every partition of every query
@@ -721,15 +763,20 @@ sky_status Runner::enqueue(BatchState& B) {
       CK(engine(bb.segs + w.seg_base + p, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_LOCAL, 1));
   }
   record(9, B);
+  CK(fork());
   for (auto& w : ws) {
     if (w.q->n == 0) continue;
+    const cudaStream_t st = qstream(w);
     CK(launch_stamp_stage(w.b.alive, w.pl.n, w.b.stage_s, ST_LOCAL, st));
   }
+  CK(join());
   record(4, B);
 
   // ---- final phase over u (sequential Sky(u), or NoSeq, Section 4.2)
+  CK(fork());
   for (auto& w : ws) {
     if (w.q->n == 0 || w.pl.P <= 1) continue;
+    const cudaStream_t st = qstream(w);
     const Plan& pl = w.pl;
     Bufs& b = w.b;
     const u64 n = pl.n;
@@ -765,11 +812,12 @@ sky_status Runner::enqueue(BatchState& B) {
       na.dom_block = pl.cfg.dom_block;
       // keep the item count within 32 bits
       while (((n / 64 + pl.P + 1) * (n / na.dom_block + 1)) >= (1ull << 31)) na.dom_block *= 2;
-      CK(launch_noseq(na, b.gcnt, b.gpre, b.scan_tmp, nu_dev, bb.ctl, st));
+      CK(launch_noseq(na, b.gcnt, b.gpre, b.scan_tmp, nu_dev, b.words + W_NOSEQ_CTR, st));
       // u is a prefix of the sorted positions' survivors: upos maps back
       CK(launch_scatter_alive(b.ualive, b.upos, n, nu_dev, b.alive, b.stage_s, ST_MERGE, st));
     }
   }
+  CK(join());
   record(10, B);
   {
     Work* first = nullptr;
@@ -786,17 +834,22 @@ sky_status Runner::enqueue(BatchState& B) {
         CK(engine(bb.msegs + w.mseg, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_MERGE, 1));
   }
   record(11, B);
+  CK(fork());
   for (auto& w : ws) {
     if (w.mseg < 0) continue;
+    const cudaStream_t st = qstream(w);
     Bufs& b = w.b;
     CK(launch_scatter_alive(b.malive, b.mpos, w.pl.n, b.words + W_NU, b.alive, b.stage_s, ST_MERGE, st));
   }
+  CK(join());
   record(5, B);
 
   // ---- output: ascending indices of Sky(r)
+  CK(fork());
   for (u32 i = 0; i < nq; ++i) {
     Work& w = ws[i];
     if (w.q->n == 0) continue;
+    const cudaStream_t st = qstream(w);
     Bufs& b = w.b;
     const u64 n = w.pl.n;
     u32* out_pid = w.q->out_pid;
@@ -809,6 +862,7 @@ sky_status Runner::enqueue(BatchState& B) {
     CK(launch_compact_idx(b.mask, b.excl, n, w.out_dev ? w.q->out_idx : b.out_dev, st));
     CK(launch_stage_hist(b.stage_s, n, b.words + W_HIST, st));
   }
+  CK(join());
   record(6, B);
   for (u32 i = 0; i < nq; ++i) {
     Work& w = ws[i];

@@ -84,6 +84,10 @@ class Runner {
   size_t pinned_words_ = 0;
   cudaEvent_t ev_[12] = {};
   cudaEvent_t gate_ev_ = nullptr;
+  static constexpr int NAUX = 4;   // streams the per-query work of a batch is spread over
+  cudaStream_t aux_[NAUX] = {};
+  cudaEvent_t fork_ev_ = nullptr;
+  cudaEvent_t join_ev_[NAUX] = {};
   sky_status ensure_ws(size_t bytes);
   sky_status ensure_pinned(size_t words);
   sky_status fail(sky_status s, const std::string& msg);
