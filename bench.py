@@ -104,6 +104,30 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+ENGINE_PROFILE = os.path.join(ROOT, "profiles", "k_engine_bench_ant1m_d6.txt")
+ENGINE_SOURCE = os.path.join(ROOT, "paper_2411_14968_gb300", "csrc", "sky_engine.cu")
+
+
+def engine_traffic():
+    """DRAM bytes (read + write) of the engine launches of one batched step,
+    from the committed ncu summary -- or None once the engine's source has
+    changed since the counters were taken."""
+    import hashlib
+    if not os.path.exists(ENGINE_PROFILE):
+        return None
+    vals = {}
+    with open(ENGINE_PROFILE) as fh:
+        for ln in fh:
+            if ln.startswith("# key ") and "=" in ln:
+                k, v = ln[len("# key "):].strip().split("=", 1)
+                vals[k.strip()] = v.strip()
+    with open(ENGINE_SOURCE, "rb") as fh:
+        src = hashlib.sha256(fh.read()).hexdigest()
+    if vals.get("engine_source_sha256") != src or "dram_bytes_per_step" not in vals:
+        return None
+    return float(vals["dram_bytes_per_step"])
+
+
 def load_workcounts():
     p = os.path.join(ROOT, "tests", "golden", "workcounts_ant_1m_d6.json")
     if not os.path.exists(p):
@@ -400,7 +424,8 @@ def gpu_arm(args, rank, world, local):
         roof = {"bound": "alu", "kernel": "k_engine (local + merge launches of the batched step)",
                 "achieved": achieved, "peak": peak, "unit": "Tcmp/s", "frac": achieved / peak,
                 "peak_source": "derived: 152 SMs x 64 FP32 compares/clk x 2.07 GHz",
-                "traffic": None, "algorithmic_tests_per_step": tests,
+                "traffic": engine_traffic(), "traffic_unit": "DRAM bytes per step (ncu, both engine launches)",
+                "algorithmic_tests_per_step": tests,
                 "kernel_ms_per_step": dom_ms_per_step,
                 "kernel_share_of_step": dom_ms_per_step / (sum(ms) / len(ms))}
 
