@@ -74,7 +74,11 @@ constexpr int R = 4;                    // candidates per lane
 constexpr int GS = 32 * R;              // candidates per warp
 constexpr int TILE = WARPS * GS;        // candidates per tile (CTA item)
 constexpr u32 DBMAX = 2048;             // dominator block capacity (points)
-constexpr u32 A_BLOCKS = 1;             // window blocks of phase A
+// Window blocks of phase A.  Must stay 1 while merges use the ordered
+// compaction: a tile's look-back runs in the item that completes the tile,
+// and only with one phase-A item per tile is that item's ticket above every
+// item of the tiles before it, so the CTAs it waits for never wait for it.
+constexpr u32 A_BLOCKS = 1;
 constexpr u64 WAIT_NS = 4000000000ull;  // bound of every wait (without progress)
 
 // Control words of a launch (zeroed by the host before it).  The queue word
