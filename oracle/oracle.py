@@ -31,7 +31,7 @@ _lock = threading.Lock()
 _lib = None
 
 RANDOM, GRID, ANGULAR, SLICED, NONE = 0, 1, 2, 3, 4
-REP_NONE, REP_SORTED = 0, 1
+REP_NONE, REP_SORTED, REP_REGION = 0, 1, 2
 MERGE_SEQUENTIAL, MERGE_NOSEQ = 0, 1
 ST_SKY, ST_GRID, ST_REP, ST_LOCAL, ST_MERGE = 1, 2, 3, 4, 5
 
@@ -66,6 +66,8 @@ def _load():
         lib.orc_sfs_all.argtypes = [P, i64, i32, P, P]
         lib.orc_sfs_all.restype = i64
         lib.orc_key_scale.argtypes = [P, i64, i32, P]
+        lib.orc_region_volume.argtypes = [P, i32, P]
+        lib.orc_region_volume.restype = ctypes.c_double
         lib.orc_assign_grid.argtypes = [P, i64, i32, P, P, P]
         lib.orc_assign_angular.argtypes = [P, i64, i32, P, P, P]
         lib.orc_splitmix64.argtypes = [u64, u64]
@@ -147,6 +149,14 @@ def key_scale(points) -> np.ndarray:
     if p.shape[0]:
         _load().orc_key_scale(_ptr(p), p.shape[0], p.shape[1], _ptr(out))
     return out
+
+
+def region_volume(point, scale=None) -> float:
+    """§4.1: volume of the dominance region of one point inside [0,1]^d
+    (attributes divided by `scale` first when given)."""
+    t = np.ascontiguousarray(point, dtype=np.float32).reshape(-1)
+    sc = None if scale is None else np.ascontiguousarray(scale, dtype=np.float32)
+    return float(_load().orc_region_volume(_ptr(t), t.shape[0], _ptr(sc) if sc is not None else None))
 
 
 def assign_grid(points, slices, normalize: bool = False) -> np.ndarray:

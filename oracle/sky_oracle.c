@@ -31,6 +31,11 @@
  *    paper's (N-1) denominator would leave the last tuple alone in partition p);
  *  - Sorted representatives: the first k points of each partition in (f, index)
  *    order; dominated representatives are removed before filtering (§4.1);
+ *  - Region representatives (§4.1, volume of the dominance region): the k
+ *    points of each partition with the largest V(t) = prod_i (1 - c_i) in
+ *    double, factors left to right, where c_i is the attribute (divided by
+ *    the column maximum when normalising) clamped to [0, 1] -- the volume of
+ *    the part of the dominance region inside the unit cube; ties by index;
  *  - NoSeq potential dominators (§4.2): Random/Angular u \ u_i; Grid the u_j
  *    whose cell is componentwise <= cell i (weak grid dominance read as <=);
  *    Sliced the u_j with j < i.
@@ -42,7 +47,7 @@
 
 /* scheme / option codes used by the oracle's entry points */
 enum { ORC_RANDOM = 0, ORC_GRID = 1, ORC_ANGULAR = 2, ORC_SLICED = 3, ORC_NONE = 4 };
-enum { ORC_REP_NONE = 0, ORC_REP_SORTED = 1 };
+enum { ORC_REP_NONE = 0, ORC_REP_SORTED = 1, ORC_REP_REGION = 2 };
 enum { ORC_MERGE_SEQUENTIAL = 0, ORC_MERGE_NOSEQ = 1 };
 /* per-point stage codes: where the point left the pipeline */
 enum {
@@ -342,6 +347,27 @@ void orc_grid_filter(const uint32_t *pid, int64_t n, int d, const uint32_t *m,
 /* ------------------------------------------------------------ Algorithm 2 */
 
 typedef struct { float f; int64_t id; } fid_t;
+typedef struct { double v; int64_t id; } vid_t;
+
+/* Descending volume, then ascending index. */
+static int cmp_vid(const void *a, const void *b) {
+  const vid_t *x = (const vid_t *)a, *y = (const vid_t *)b;
+  if (x->v > y->v) return -1;
+  if (x->v < y->v) return 1;
+  return (x->id < y->id) ? -1 : (x->id > y->id);
+}
+
+/* §4.1: hyper-volume of the dominance region of t within [0,1]^d. */
+double orc_region_volume(const float *t, int d, const float *scale) {
+  double v = 1.0;
+  for (int a = 0; a < d; ++a) {
+    double c = (double)key_coord(t, a, scale);
+    if (c < 0.0) c = 0.0;
+    if (c > 1.0) c = 1.0;
+    v = v * (1.0 - c);
+  }
+  return v;
+}
 
 static int cmp_fid(const void *a, const void *b) {
   const fid_t *x = (const fid_t *)a, *y = (const fid_t *)b;
@@ -367,17 +393,19 @@ int64_t orc_partitioned(const float *pts, int64_t n, int d, int scheme, uint32_t
   uint64_t P = 1;
   float scale[8];
   const float *sc = NULL;
-  if (normalize && (scheme == ORC_GRID || scheme == ORC_ANGULAR)) {
+  if (normalize && (scheme == ORC_GRID || scheme == ORC_ANGULAR || rep == ORC_REP_REGION)) {
     orc_key_scale(pts, n, d, scale);
     sc = scale;
   }
+  /* the partition keys use the scale only for Grid and Angular */
+  const float *key_sc = (scheme == ORC_GRID || scheme == ORC_ANGULAR) ? sc : NULL;
   /* Partition(r, p): Alg. 2 first phase */
   if (scheme == ORC_GRID) {
     for (int a = 0; a < d; ++a) P *= slices[a];
-    orc_assign_grid(pts, n, d, slices, sc, pid);
+    orc_assign_grid(pts, n, d, slices, key_sc, pid);
   } else if (scheme == ORC_ANGULAR) {
     for (int a = 0; a + 1 < d; ++a) P *= slices[a];
-    orc_assign_angular(pts, n, d, slices, sc, pid);
+    orc_assign_angular(pts, n, d, slices, key_sc, pid);
   } else if (scheme == ORC_RANDOM || scheme == ORC_SLICED) {
     P = p < 1 ? 1 : p;
     if (P > (uint64_t)n) P = (uint64_t)n;
@@ -409,24 +437,36 @@ int64_t orc_partitioned(const float *pts, int64_t n, int d, int scheme, uint32_t
   for (int64_t i = 0; i < n; ++i)
     if (!stage[i]) mem[fill[pid[i]]++] = i;
 
-  /* Sorted representatives (§4.1): first k tuples of every partition in
-     (f, index) order; dominated representatives are discarded, then every
-     tuple a remaining representative dominates is deleted. */
-  if (rep == ORC_REP_SORTED) {
+  /* Representatives (§4.1): Sorted = first k tuples of every partition in
+     (f, index) order; Region = the k tuples of largest dominance-region
+     volume.  Dominated representatives are discarded, then every tuple a
+     remaining representative dominates is deleted. */
+  if (rep == ORC_REP_SORTED || rep == ORC_REP_REGION) {
     uint32_t k = reps_per_partition < 1 ? 1 : reps_per_partition;
     int64_t *reps = (int64_t *)malloc((size_t)(P * k + 1) * sizeof(int64_t));
     int64_t nrep = 0;
     for (uint64_t q = 0; q < P; ++q) {
       int64_t len = cnt[q + 1] - cnt[q];
       if (len == 0) continue;
-      fid_t *o = (fid_t *)malloc((size_t)len * sizeof(fid_t));
-      for (int64_t j = 0; j < len; ++j) {
-        o[j].id = mem[cnt[q] + j];
-        o[j].f = score_of(pts + o[j].id * d, d);
+      if (rep == ORC_REP_SORTED) {
+        fid_t *o = (fid_t *)malloc((size_t)len * sizeof(fid_t));
+        for (int64_t j = 0; j < len; ++j) {
+          o[j].id = mem[cnt[q] + j];
+          o[j].f = score_of(pts + o[j].id * d, d);
+        }
+        qsort(o, (size_t)len, sizeof(fid_t), cmp_fid);
+        for (int64_t j = 0; j < len && j < (int64_t)k; ++j) reps[nrep++] = o[j].id;
+        free(o);
+      } else {
+        vid_t *o = (vid_t *)malloc((size_t)len * sizeof(vid_t));
+        for (int64_t j = 0; j < len; ++j) {
+          o[j].id = mem[cnt[q] + j];
+          o[j].v = orc_region_volume(pts + o[j].id * d, d, sc);
+        }
+        qsort(o, (size_t)len, sizeof(vid_t), cmp_vid);
+        for (int64_t j = 0; j < len && j < (int64_t)k; ++j) reps[nrep++] = o[j].id;
+        free(o);
       }
-      qsort(o, (size_t)len, sizeof(fid_t), cmp_fid);
-      for (int64_t j = 0; j < len && j < (int64_t)k; ++j) reps[nrep++] = o[j].id;
-      free(o);
     }
     uint8_t *rep_kept = (uint8_t *)malloc((size_t)(nrep + 1));
     for (int64_t a = 0; a < nrep; ++a) {

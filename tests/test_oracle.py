@@ -325,7 +325,7 @@ def test_partitioned_equals_skyline(oracle_mod, kind, d):
             kw["slices"] = [2] * d if d > 3 else [3] * d
         if name == "angular":
             kw["slices"] = ([3, 2, 2, 2, 2, 2, 2][: d - 1]) if d > 1 else []
-        for rep in (0, 1):
+        for rep in (0, 1, 2):
             for merge in (0, 1):
                 r = oracle_mod.partitioned(x, normalize=norm, rep=rep, merge=merge, **kw)
                 np.testing.assert_array_equal(r["indices"], want, err_msg=f"{name} rep={rep} merge={merge}")
@@ -356,6 +356,47 @@ def test_partitioned_edge_cases(oracle_mod):
     x = np.full((100, 4), 0.5, np.float32)
     r = oracle_mod.partitioned(x, scheme=3, p=10, rep=1, merge=1)
     np.testing.assert_array_equal(r["indices"], np.arange(100))
+
+
+def test_region_volume_hand_values(oracle_mod):
+    # §4.1: V = prod (1 - t[i]) over [0,1]; attributes outside [0,1] are
+    # clamped (the part of the dominance region inside the unit cube)
+    assert oracle_mod.region_volume([0.5, 0.2]) == pytest.approx(0.4)
+    assert oracle_mod.region_volume([0.0, 0.0, 0.0]) == 1.0
+    assert oracle_mod.region_volume([1.2, -0.3, 0.25]) == 0.0
+    assert oracle_mod.region_volume([-0.5, 0.75]) == pytest.approx(0.25)
+    assert oracle_mod.region_volume([1.0, 1.0], scale=[2.0, 2.0]) == pytest.approx(0.25)
+
+
+def test_region_volume_is_dominance_region_measure(oracle_mod):
+    # independent pin: the volume equals the fraction of uniform points of the
+    # unit cube that t dominates (Monte Carlo, 4 standard errors)
+    rng = np.random.default_rng(3)
+    u = rng.random((200_000, 3)).astype(np.float32)
+    for t in ([0.2, 0.5, 0.1], [0.7, 0.05, 0.3], [0.33, 0.33, 0.33]):
+        frac = np.mean(np.all(u >= np.float32(t), axis=1))
+        v = oracle_mod.region_volume(t)
+        assert abs(frac - v) < 4 * np.sqrt(v * (1 - v) / u.shape[0]) + 1e-9, (t, frac, v)
+
+
+def test_region_representatives_differ_from_sorted(oracle_mod):
+    # one partition: A has the lowest score (the Sorted representative), B
+    # the largest dominance region (the Region representative); C is
+    # dominated by B only, D by A only, E by neither
+    x = np.array([[0.10, 0.70],   # A: score 0.80, V = 0.9 * 0.3 = 0.27
+                  [0.40, 0.45],   # B: score 0.85, V = 0.6 * 0.55 = 0.33
+                  [0.50, 0.50],   # C
+                  [0.15, 0.90],   # D
+                  [0.05, 0.99]], np.float32)  # E (skyline)
+    srt = oracle_mod.partitioned(x, rep=oracle_mod.REP_SORTED)
+    reg = oracle_mod.partitioned(x, rep=oracle_mod.REP_REGION)
+    np.testing.assert_array_equal(srt["indices"], [0, 1, 4])
+    np.testing.assert_array_equal(reg["indices"], [0, 1, 4])
+    assert srt["stage"][3] == oracle_mod.ST_REP and srt["stage"][2] == oracle_mod.ST_LOCAL
+    assert reg["stage"][2] == oracle_mod.ST_REP and reg["stage"][3] == oracle_mod.ST_LOCAL
+    # k = 2 Region representatives per partition: both B and A
+    reg2 = oracle_mod.partitioned(x, rep=oracle_mod.REP_REGION, reps_per_partition=2)
+    assert reg2["stage"][2] == oracle_mod.ST_REP and reg2["stage"][3] == oracle_mod.ST_REP
 
 
 def test_grid_filter_drops_in_pipeline(oracle_mod):
