@@ -493,6 +493,96 @@ def gpu_arm(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def rep_filtering_experiment(local: int):
+    """Section 5 (Figure: effectiveness of representative filtering): the
+    share of tuples that Sorted and Region representatives discard, on
+    uniform, correlated and anticorrelated data with d = 4, under each
+    partitioning scheme with 1 representative per partition."""
+    import torch
+    from paper_2411_14968_gb300 import datagen, native
+    n, d = 1_000_000, 4
+    data = {"uniform": datagen.independent(n, d, 41, quantised=False),
+            "correlated": datagen.correlated(n, d, 42, quantised=False),
+            "anticorrelated": datagen.anticorrelated(n, d, 43)}
+    schemes = {"random": dict(scheme="random", p=64, seed=1), "grid": dict(scheme="grid", slices=[2] * d),
+               "angular": dict(scheme="angular", slices=[4, 4, 4]), "sliced": dict(scheme="sliced", p=64)}
+    out = {}
+    with native.Context(local) as ctx:
+        for dname, x in data.items():
+            xt = torch.from_numpy(x).cuda()
+            for sname, kw in schemes.items():
+                row = {}
+                sky = None
+                for rep in ("sorted", "region"):
+                    r = ctx.skyline(xt, params=native.make_params(rep=rep, grid_filter=False, **kw))
+                    st = ctx.stats()
+                    row[rep] = round(100.0 * st["rep_dropped"] / n, 2)
+                    sky = int(r.shape[0]) if sky is None else sky
+                    assert sky == int(r.shape[0])  # the result never depends on the representatives
+                out[f"{dname}/{sname}"] = row
+    print(json.dumps({"experiment": "representative filtering, % of tuples discarded (N=1e6, d=4, 1 rep per "
+                                    "partition, Grid Filtering off)", "results": out}), flush=True)
+
+
+def sweeps_experiment(local: int):
+    """Section 5 (operating-parameter sweeps on anticorrelated data, defaults
+    N = 1M, d = 4, p = 120): GPU time of the global skyline and the size of
+    the local-skyline union for the plain strategies and the improved ones,
+    varying N, d and p one at a time.  Grid and Angular reach p = 120 with
+    per-dimension / per-angle slice counts (2,3,4,5) and (6,5,4)."""
+    import torch
+    from paper_2411_14968_gb300 import datagen, native
+
+    def strategies(d, p):
+        ang = {4: [6, 5, 4], 2: [p], 3: [12, 10]}.get(d)
+        if ang is None:  # closest product to p with d - 1 factors of 2..6
+            ang = [2] * (d - 1)
+            i = 0
+            while int(np.prod(ang)) * 2 <= p:
+                ang[i % (d - 1)] += 1
+                i += 1
+        grid = [2, 3, 4, 5] if d == 4 else [2] * d
+        return {
+            "random": dict(scheme="random", p=p, seed=1), "grid": dict(scheme="grid", slices=grid),
+            "angular": dict(scheme="angular", slices=ang), "sliced": dict(scheme="sliced", p=p),
+            "sliced+": dict(scheme="sliced", p=p, rep="sorted"),
+            "angular+": dict(scheme="angular", slices=ang, rep="sorted"),
+            "noseq": dict(scheme="sliced", p=p, rep="sorted", merge="noseq"),
+        }
+
+    rows = []
+    with native.Context(local) as ctx:
+        ctx.set_timing(True)
+
+        def run(x, d, p, names, tag):
+            xt = torch.from_numpy(x).cuda()
+            strat = strategies(d, p)
+            sky = None
+            for name in names:
+                pr = native.make_params(**strat[name])
+                ctx.skyline(xt, params=pr)  # warm-up (workspace)
+                ms = []
+                for _ in range(2):
+                    r = ctx.skyline(xt, params=pr)
+                    ms.append(ctx.stats()["ms_total"])
+                st = ctx.stats()
+                sky = int(r.shape[0]) if sky is None else sky
+                assert sky == int(r.shape[0])
+                rows.append({"sweep": tag, "n": x.shape[0], "d": d, "p": st["partitions"], "strategy": name,
+                             "ms": round(min(ms), 3), "local_union": st["local_union"], "skyline": sky})
+                print(json.dumps(rows[-1]), flush=True)
+
+        plain = ["random", "grid", "angular", "sliced"]
+        improved = ["sliced+", "angular+", "noseq"]
+        for n in (100_000, 500_000, 1_000_000, 5_000_000, 10_000_000):
+            run(datagen.anticorrelated(n, 4, 7), 4, 120, plain + improved, "size")
+        for d in (2, 3, 5, 6, 7):
+            run(datagen.anticorrelated(1_000_000, d, 8), d, 120, improved, "dimensions")
+        for p in (60, 240, 480, 720, 1200, 2400, 3600):
+            run(datagen.anticorrelated(1_000_000, 4, 7), 4, p, ["sliced+", "noseq"], "partitions")
+    print(json.dumps({"experiment": "sweeps (anticorrelated; defaults N=1e6, d=4, p=120)", "rows": rows}), flush=True)
+
+
 def ncu_case(which: str):
     """The cases the engine's ncu captures run: the two k_engine launches
     (local phase, merge) of the second call are the captured ones."""
@@ -524,6 +614,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--experiment", choices=["rep-filtering", "sweeps"], default=None,
+                    help="run one of the paper's experiments instead of the benchmark")
     ap.add_argument("--ncu-case", choices=["small", "batch"], default=None,
                     help="run a profiling case only, twice, default knobs, no timing: 'small' = one query "
                          "(anticorrelated N=200k, d=6, Sliced p=64); 'batch' = the benchmark's batched step")
@@ -534,6 +626,12 @@ def main():
     rank, world, local = dist_env()
     if args.ncu_case:
         ncu_case(args.ncu_case)
+        return
+    if args.experiment == "rep-filtering":
+        rep_filtering_experiment(local)
+        return
+    if args.experiment == "sweeps":
+        sweeps_experiment(local)
         return
     if args.impl == "reference":
         reference_arm(args, rank, world)

@@ -61,7 +61,12 @@ typedef enum {
   SKY_NONE = 4      /* one partition: plain SFS (Algorithm 1) over the whole input */
 } sky_partitioning;
 
-typedef enum { SKY_REP_NONE = 0, SKY_REP_SORTED = 1 } sky_rep;
+/* Representative filtering (Section 4.1): Sorted = the first points of each
+   partition in score order; Region = the points with the largest volume of
+   the dominance region inside the unit cube (prod (1 - x_i), attributes
+   clamped to [0, 1], or divided by the column maximum first when
+   `normalize` is set; at most 64 per partition). */
+typedef enum { SKY_REP_NONE = 0, SKY_REP_SORTED = 1, SKY_REP_REGION = 2 } sky_rep;
 typedef enum { SKY_MERGE_SEQUENTIAL = 0, SKY_MERGE_NOSEQ = 1 } sky_merge;
 typedef enum {
   SKY_EXEC_PERSISTENT = 0, /* all partitions' local skylines in one cooperative launch */
@@ -73,8 +78,8 @@ typedef struct {
   sky_partitioning scheme;
   uint32_t num_partitions;     /* Random / Sliced: p (clamped to [1, N]) */
   uint32_t slices[8];          /* Grid: m per attribute (d used); Angular: m per angle (d-1 used) */
-  uint32_t normalize;          /* Grid / Angular: divide each attribute by its column maximum
-                                  for the partition key only (dominance uses raw values) */
+  uint32_t normalize;          /* Grid / Angular keys and Region volumes: divide each attribute by
+                                  its column maximum first (dominance uses raw values) */
   uint32_t slice_dim;          /* Sliced: attribute to slice on (default 0) */
   uint64_t seed;               /* Random: SplitMix64 seed */
   uint32_t grid_filter;        /* Grid: drop cells a non-empty cell grid-dominates (default 1) */

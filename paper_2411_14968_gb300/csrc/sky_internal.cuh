@@ -143,6 +143,11 @@ cudaError_t launch_grid_filter(const u32* seg_off, const u32* spid, u64 n, int d
 // rep_alive 0.
 cudaError_t launch_rep_select(const u32* seg_off, u32 P, u32 k, const u8* dropped, const float* pts,
                               int d, float* rep_pts, u8* rep_alive, cudaStream_t st);
+// Region representatives (Section 4.1): per segment the k points of largest
+// dominance-region volume inside [0,1]^d (orig breaks ties); colmax (fkey
+// column maxima) scales the attributes when normalize is set.
+cudaError_t launch_rep_region(const u32* seg_off, u32 P, u32 k, const u8* dropped, const float* pts, const u32* orig,
+                              const u32* colmax, int normalize, int d, float* rep_pts, u8* rep_alive, cudaStream_t st);
 
 // Compaction of the points alive after the local phase into u (keeps the
 // (partition, score, index) order).

@@ -216,8 +216,8 @@ sky_status validate(const float* points, u64 n, u32 d, const sky_params* pa, Pla
   pl->scheme = (int)p.scheme;
   pl->normalize = p.normalize ? 1 : 0;
   pl->seed = p.seed;
-  pl->rep = p.rep == SKY_REP_SORTED ? 1 : 0;
-  if (p.rep != SKY_REP_NONE && p.rep != SKY_REP_SORTED) return bad("unknown rep mode");
+  pl->rep = (int)p.rep;
+  if (p.rep != SKY_REP_NONE && p.rep != SKY_REP_SORTED && p.rep != SKY_REP_REGION) return bad("unknown rep mode");
   pl->k = p.reps_per_partition ? p.reps_per_partition : 1;
   if (p.merge != SKY_MERGE_SEQUENTIAL && p.merge != SKY_MERGE_NOSEQ) return bad("unknown merge");
   pl->merge = (int)p.merge;
@@ -260,6 +260,7 @@ sky_status validate(const float* points, u64 n, u32 d, const sky_params* pa, Pla
   }
   pl->P = (u32)P;
   if (pl->rep && (u64)pl->P * pl->k > (1u << 22)) return bad("too many representatives");
+  if (pl->rep == SKY_REP_REGION && pl->k > 64) return bad("at most 64 Region representatives per partition");
   pl->pid_bits = bits_for(P);
   pl->cfg.chunk_min = p.chunk_min ? p.chunk_min : DEFAULT_CHUNK_MIN;
   pl->cfg.chunk_max = p.chunk_max ? p.chunk_max : DEFAULT_CHUNK_MAX;
@@ -635,7 +636,10 @@ sky_status Runner::enqueue(BatchState& B) {
     pr.keys = b.keys[0];
     pr.vals = b.vals[0];
     pr.err = err;
-    if (pr.normalize) CK(launch_colmax(w.X, n, D, b.words + W_COLMAX, err, st));
+    // column maxima: keys of normalised Grid / Angular, volumes of normalised
+    // Region representatives
+    if (pr.normalize || (pl.normalize && pl.rep == SKY_REP_REGION))
+      CK(launch_colmax(w.X, n, D, b.words + W_COLMAX, err, st));
     CK(launch_prep(pr, D, st));
     int sel = 0;
     if (pl.scheme == SCHEME_RANDOM || pl.scheme == SCHEME_SLICED) {
@@ -694,7 +698,11 @@ sky_status Runner::enqueue(BatchState& B) {
     }
     if (pl.rep) {
       u32 nrep = P * pl.k;
-      CK(launch_rep_select(b.seg_off, P, pl.k, w.dropped, b.pts, D, b.rep_pts, b.rep_alive, st));
+      if (pl.rep == SKY_REP_REGION)
+        CK(launch_rep_region(b.seg_off, P, pl.k, w.dropped, b.pts, b.orig, b.words + W_COLMAX, pl.normalize, D,
+                             b.rep_pts, b.rep_alive, st));
+      else
+        CK(launch_rep_select(b.seg_off, P, pl.k, w.dropped, b.pts, D, b.rep_pts, b.rep_alive, st));
       // R = Sky(reps): dominated representatives are discarded first
       CK(launch_relative(b.rep_pts, b.rep_alive, nrep, b.rep_pts, nrep, nullptr, D, st));
       CK(scan_u8(b.rep_alive, b.rep_excl, nrep, true, b.scan_tmp, st));

@@ -313,6 +313,113 @@ __global__ void k_rep_select(const u32* __restrict__ seg_off, u32 P, u32 k,
   for (int v = 0; v < V; ++v) dst[v] = ok ? src[(u64)(seg_off[s] + j) * V + v] : inf;
 }
 
+// Region representatives (Section 4.1): the k points of each segment with
+// the largest volume of the dominance region inside the unit cube, V(t) =
+// prod (1 - c_a) in double, factors left to right, c_a the attribute (over
+// the column scale when normalising) clamped to [0, 1]; ties by original
+// index.  One block per segment; pass r finds the best point after the
+// winner of pass r - 1 in the order (V descending, index ascending).
+__device__ __forceinline__ bool region_better(double v, u32 id, double bv, u32 bid) {
+  return v > bv || (v == bv && id < bid);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_rep_region(const u32* __restrict__ seg_off, u32 P, u32 k,
+                                                    const u8* __restrict__ dropped, const float* __restrict__ pts,
+                                                    const u32* __restrict__ orig, const u32* __restrict__ colmax,
+                                                    int normalize, float* __restrict__ rep_pts,
+                                                    u8* __restrict__ rep_alive) {
+  __shared__ double s_v[8];
+  __shared__ u32 s_id[8], s_pos[8];
+  __shared__ double s_limv;
+  __shared__ u32 s_limid;
+  constexpr int V = vec_of(D);
+  const u32 s = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const u32 o = seg_off[s];
+  const u32 len = (dropped && dropped[s]) ? 0u : seg_off[s + 1] - o;
+  float sc[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) sc[a] = 1.0f;
+  if (normalize) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      float mx = fkey_inv(colmax[a]);
+      sc[a] = (mx > 0.0f && mx <= 3.402823466e38f) ? mx : 1.0f;
+    }
+  }
+  const float4* src = reinterpret_cast<const float4*>(pts);
+  bool have_lim = false;
+  double limv = 0.0;
+  u32 limid = 0;
+  for (u32 r = 0; r < k; ++r) {
+    double bv = -1.0;
+    u32 bid = 0xffffffffu, bpos = 0xffffffffu;
+    for (u32 j = threadIdx.x; j < len; j += blockDim.x) {
+      float x[8];
+      float4 q0 = src[(u64)(o + j) * V];
+      x[0] = q0.x; x[1] = q0.y; x[2] = q0.z; x[3] = q0.w;
+      if (V > 1) {
+        float4 q1 = src[(u64)(o + j) * V + 1];
+        x[4] = q1.x; x[5] = q1.y; x[6] = q1.z; x[7] = q1.w;
+      }
+      double v = 1.0;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        double c = normalize ? (double)__fdiv_rn(x[a], sc[a]) : (double)x[a];
+        c = c < 0.0 ? 0.0 : (c > 1.0 ? 1.0 : c);
+        v = __dmul_rn(v, 1.0 - c);
+      }
+      const u32 id = orig[o + j];
+      const bool after = !have_lim || v < limv || (v == limv && id > limid);
+      if (after && region_better(v, id, bv, bid)) {
+        bv = v;
+        bid = id;
+        bpos = o + j;
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      double ov = __shfl_down_sync(FULL, bv, off);
+      u32 oid = __shfl_down_sync(FULL, bid, off);
+      u32 opos = __shfl_down_sync(FULL, bpos, off);
+      if (region_better(ov, oid, bv, bid)) {
+        bv = ov;
+        bid = oid;
+        bpos = opos;
+      }
+    }
+    if (lane == 0) {
+      s_v[warp] = bv;
+      s_id[warp] = bid;
+      s_pos[warp] = bpos;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (region_better(s_v[w], s_id[w], bv, bid)) {
+          bv = s_v[w];
+          bid = s_id[w];
+          bpos = s_pos[w];
+        }
+      const u64 t = (u64)s * k + r;
+      const bool ok = bpos != 0xffffffffu;
+      rep_alive[t] = ok ? 1 : 0;
+      float4* dst = reinterpret_cast<float4*>(rep_pts) + t * V;
+      const float4 inf = make_float4(INFINITY, INFINITY, INFINITY, INFINITY);
+#pragma unroll
+      for (int v = 0; v < V; ++v) dst[v] = ok ? src[(u64)bpos * V + v] : inf;
+      s_limv = bv;
+      s_limid = bid;
+    }
+    __syncthreads();
+    have_lim = true;
+    limv = s_limv;
+    limid = s_limid;
+    __syncthreads();
+  }
+}
+
 // Kept representatives packed after R = Sky(reps) was computed in place.
 template <int D>
 __global__ void k_compact_reps(const u8* __restrict__ rep_alive, const u32* __restrict__ excl, u32 nrep,
@@ -506,6 +613,16 @@ cudaError_t launch_rep_select(const u32* seg_off, u32 P, u32 k, const u8* droppe
   return dispatch_d(d, [&](auto D) {
     note_launch();
     k_rep_select<decltype(D)::value><<<grid_for(cnt), PT, 0, st>>>(seg_off, P, k, dropped, pts, rep_pts, rep_alive);
+  });
+}
+
+cudaError_t launch_rep_region(const u32* seg_off, u32 P, u32 k, const u8* dropped, const float* pts, const u32* orig,
+                              const u32* colmax, int normalize, int d, float* rep_pts, u8* rep_alive, cudaStream_t st) {
+  if (P == 0 || k == 0) return cudaSuccess;
+  return dispatch_d(d, [&](auto D) {
+    note_launch();
+    k_rep_region<decltype(D)::value><<<P, 256, 0, st>>>(seg_off, P, k, dropped, pts, orig, colmax, normalize, rep_pts,
+                                                         rep_alive);
   });
 }
 

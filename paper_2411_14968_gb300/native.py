@@ -18,7 +18,7 @@ from . import build as _build
 
 SKY_OK, SKY_EINVAL, SKY_ENOMEM, SKY_ECUDA, SKY_ETIMEOUT, SKY_EBUSY, SKY_ECANCELLED = range(7)
 SCHEMES = {"random": 0, "grid": 1, "angular": 2, "sliced": 3, "none": 4}
-REPS = {"none": 0, "sorted": 1}
+REPS = {"none": 0, "sorted": 1, "region": 2}
 MERGES = {"sequential": 0, "noseq": 1}
 EXECS = {"persistent": 0, "plain": 1}
 STAGE_SKY, STAGE_GRID, STAGE_REP, STAGE_LOCAL, STAGE_MERGE = 1, 2, 3, 4, 5

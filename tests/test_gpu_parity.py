@@ -27,15 +27,17 @@ def _oracle_kw(scheme, p, slices, normalize, rep, merge, seed=0, slice_dim=0, gr
     from oracle import oracle as O
     return dict(scheme={"random": O.RANDOM, "grid": O.GRID, "angular": O.ANGULAR, "sliced": O.SLICED,
                         "none": O.NONE}[scheme], p=p, slices=slices, normalize=normalize, seed=seed,
-                rep={"none": 0, "sorted": 1}[rep], merge={"sequential": 0, "noseq": 1}[merge],
+                rep={"none": 0, "sorted": 1, "region": 2}[rep], merge={"sequential": 0, "noseq": 1}[merge],
                 slice_dim=slice_dim, grid_filter=grid_filter)
 
 
 def _check(ctx, oracle_mod, x, scheme="none", p=1, slices=None, normalize=False, rep="none",
-           merge="sequential", exec="persistent", seed=0, slice_dim=0, **tune):
-    want = oracle_mod.partitioned(x, **_oracle_kw(scheme, p, slices, normalize, rep, merge, seed, slice_dim))
+           merge="sequential", exec="persistent", seed=0, slice_dim=0, reps_per_partition=1, **tune):
+    want = oracle_mod.partitioned(x, reps_per_partition=reps_per_partition,
+                                  **_oracle_kw(scheme, p, slices, normalize, rep, merge, seed, slice_dim))
     idx, pid, stage = ctx.skyline(x, scheme=scheme, p=p, slices=slices, normalize=normalize, rep=rep,
-                                  merge=merge, exec=exec, seed=seed, slice_dim=slice_dim, with_diag=True, **tune)
+                                  merge=merge, exec=exec, seed=seed, slice_dim=slice_dim, with_diag=True,
+                                  reps_per_partition=reps_per_partition, **tune)
     tag = f"{scheme} p={p} slices={slices} rep={rep} merge={merge} exec={exec}"
     np.testing.assert_array_equal(idx, want["indices"], err_msg=tag)
     np.testing.assert_array_equal(pid, want["pid"], err_msg=tag + " pid")
@@ -74,9 +76,22 @@ def test_all_schemes(ctx, oracle_mod, kind, d):
             if d == 1:
                 continue
             slices = ([4, 3, 2, 2, 2, 2, 2])[: d - 1]
-        for rep in ("none", "sorted"):
+        for rep in ("none", "sorted", "region"):
             for merge in ("sequential", "noseq"):
                 _check(ctx, oracle_mod, x, scheme, p, slices, norm, rep, merge, seed=7)
+
+
+def test_several_representatives_per_partition(ctx, oracle_mod):
+    # k > 1 Sorted and Region representatives (Section 4.1), with ties of
+    # volume (quantised data) broken by index, and normalised volumes on data
+    # outside [0, 1]
+    x = datagen.independent(20000, 4, 21)
+    y = datagen.make("skewed", 8000, 5, 22)
+    for rep in ("sorted", "region"):
+        for k in (2, 7):
+            _check(ctx, oracle_mod, x, "sliced", 9, rep=rep, reps_per_partition=k)
+            _check(ctx, oracle_mod, y, "random", 5, normalize=True, rep=rep, reps_per_partition=k, seed=3)
+    _check(ctx, oracle_mod, y, "angular", 1, [3, 2, 2, 2], normalize=False, rep="region", reps_per_partition=3)
 
 
 def test_multi_round_small_chunks(ctx, oracle_mod):
