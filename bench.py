@@ -583,6 +583,57 @@ def sweeps_experiment(local: int):
     print(json.dumps({"experiment": "sweeps (anticorrelated; defaults N=1e6, d=4, p=120)", "rows": rows}), flush=True)
 
 
+def configs_experiment(local: int):
+    """Throughput of the other workload configurations (points per second,
+    one query at a time and as one batch, CUDA events), beside the headline
+    one: the tiny Grid case; 4M-point d = 8 quantised independent and
+    correlated data, Grid m = 2 (256 cells) vs Random p = 256; 2M-point
+    skewed record-like data, Angular p = 128 with Sorted representatives,
+    NoSeq vs the sequential final phase."""
+    import torch
+    from paper_2411_14968_gb300 import datagen, native
+    cases = [
+        ("anticorrelated N=1e4 d=4, Grid m=2 (16 cells)", ("anticorrelated", 10_000, 4, 1),
+         [dict(scheme="grid", slices=[2] * 4)]),
+        ("independent quantised N=4e6 d=8, Grid m=2 vs Random p=256", ("independent", 4_000_000, 8, 3),
+         [dict(scheme="grid", slices=[2] * 8), dict(scheme="random", p=256, seed=11)]),
+        ("correlated quantised N=4e6 d=8, Grid m=2 vs Random p=256", ("correlated", 4_000_000, 8, 3),
+         [dict(scheme="grid", slices=[2] * 8), dict(scheme="random", p=256, seed=11)]),
+        ("skewed N=2e6 d=6, Angular (4,4,2,2,2) + Sorted reps, sequential vs NoSeq", ("skewed", 2_000_000, 6, 4),
+         [dict(scheme="angular", slices=[4, 4, 2, 2, 2], normalize=True, rep="sorted"),
+          dict(scheme="angular", slices=[4, 4, 2, 2, 2], normalize=True, rep="sorted", merge="noseq")]),
+    ]
+    out = []
+    with native.Context(local) as ctx:
+        ctx.set_timing(True)
+        for title, (kind, n, d, seed), variants in cases:
+            xt = torch.from_numpy(datagen.make(kind, n, d, seed)).cuda()
+            row = {"config": title, "variants": []}
+            for kw in variants:
+                p = native.make_params(**kw)
+                ctx.skyline(xt, params=p)
+                ms = []
+                for _ in range(3):
+                    r = ctx.skyline(xt, params=p)
+                    ms.append(ctx.stats()["ms_total"])
+                st = ctx.stats()
+                row["variants"].append({"params": kw, "ms": round(min(ms), 3),
+                                        "points_per_s": n / (min(ms) * 1e-3), "skyline": int(r.shape[0]),
+                                        "local_union": st["local_union"]})
+            if len(variants) > 1:
+                ps = [native.make_params(**kw) for kw in variants]
+                ctx.skyline_batch([(xt, p) for p in ps])
+                bms = []
+                for _ in range(3):
+                    ctx.skyline_batch([(xt, p) for p in ps])
+                    bms.append(ctx.stats()["ms_total"])
+                row["batched"] = {"ms": round(min(bms), 3),
+                                  "points_per_s": n * len(variants) / (min(bms) * 1e-3)}
+            out.append(row)
+            print(json.dumps(row), flush=True)
+    print(json.dumps({"experiment": "workload configurations", "rows": out}), flush=True)
+
+
 def ncu_case(which: str):
     """The cases the engine's ncu captures run: the two k_engine launches
     (local phase, merge) of the second call are the captured ones."""
@@ -614,7 +665,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--experiment", choices=["rep-filtering", "sweeps"], default=None,
+    ap.add_argument("--experiment", choices=["rep-filtering", "sweeps", "configs"], default=None,
                     help="run one of the paper's experiments instead of the benchmark")
     ap.add_argument("--ncu-case", choices=["small", "batch"], default=None,
                     help="run a profiling case only, twice, default knobs, no timing: 'small' = one query "
@@ -632,6 +683,9 @@ def main():
         return
     if args.experiment == "sweeps":
         sweeps_experiment(local)
+        return
+    if args.experiment == "configs":
+        configs_experiment(local)
         return
     if args.impl == "reference":
         reference_arm(args, rank, world)
