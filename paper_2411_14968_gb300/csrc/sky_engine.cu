@@ -185,13 +185,16 @@ constexpr int SCAN_U = 4;               // dominators per step of the scan loop
 constexpr u32 NEG_INF2 = 0xFC00FC00u;  // (-inf, -inf)
 constexpr u32 POS_INF2 = 0x7C007C00u;  // (+inf, +inf)
 
-// The candidates of one lane.
-struct Cands {
-  uint4 c[R];    // FP16 images (-inf when dead)
-  u32 pos[R];    // segment-relative position
-  bool alive[R];
-  bool was[R];
+// The candidates of one lane: RR slots (R when an item starts; fewer once
+// the warp's live candidates have been compacted).
+template <int RR>
+struct CandsT {
+  uint4 c[RR];    // FP16 images (-inf when dead)
+  u32 pos[RR];    // segment-relative position
+  bool alive[RR];
+  bool was[RR];
 };
+using Cands = CandsT<R>;
 
 // Where the FP32 attributes of dominator j of a staged block live: win[base
 // + j] (window) or pts[map[base + j]] (dense list).
@@ -209,15 +212,67 @@ __device__ __forceinline__ const float4* dom_fp32(const DomSrc& s, u32 j) {
   return s.fp32 + (u64)idx * V;
 }
 
-// Scans the staged block sb[0..cnt) for the warp's candidates.
-template <int D>
-__device__ __forceinline__ void scan_smem(const uint4* sb, u32 cnt, const DomSrc& src, const float4* pts,
-                                          Cands& c) {
+template <int RR>
+__device__ __forceinline__ u32 alive_count(const CandsT<RR>& c) {
+  u32 n = 0;
+#pragma unroll
+  for (int r = 0; r < RR; ++r) n += __popc(__ballot_sync(FULL, c.alive[r]));
+  return n;
+}
+
+// Records the warp's kills (candidates alive at load, dead now).
+template <int RR>
+__device__ __forceinline__ void write_kills(const CandsT<RR>& c, u8* alive) {
+#pragma unroll
+  for (int r = 0; r < RR; ++r)
+    if (c.was[r] && !c.alive[r]) alive[c.pos[r]] = 0;
+}
+
+// Moves the warp's live candidates (at most 32 x RB of them) into RB slots
+// per lane, in slot-major order, through the warp's shared scratch; kills
+// are recorded first.
+template <int RA, int RB>
+__device__ __forceinline__ void compact(const CandsT<RA>& a, CandsT<RB>& b, uint4* sc, u32* sp, u8* alive) {
+  const int lane = threadIdx.x & 31;
+  const u32 lt = (1u << lane) - 1u;
+  write_kills(a, alive);
+  u32 k0 = 0;
+#pragma unroll
+  for (int r = 0; r < RA; ++r) {
+    const u32 m = __ballot_sync(FULL, a.alive[r]);
+    if (a.alive[r]) {
+      const u32 k = k0 + __popc(m & lt);
+      sc[k] = a.c[r];
+      sp[k] = a.pos[r];
+    }
+    k0 += __popc(m);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < RB; ++r) {
+    const u32 k = r * 32 + lane;
+    const bool v = k < k0;
+    b.alive[r] = v;
+    b.was[r] = v;
+    b.c[r] = v ? sc[k] : make_uint4(NEG_INF2, NEG_INF2, NEG_INF2, NEG_INF2);
+    b.pos[r] = v ? sp[k] : 0u;
+  }
+  __syncwarp();
+}
+
+// Scans the staged block sb[j..cnt) for the warp's candidates, RR slots per
+// lane.  Every 32 dominators the warp counts its live candidates; it stops
+// early when none is left or when they fit in half the slots (the caller
+// compacts them and goes on with fewer slots, so dead lanes stop costing
+// compares).  Returns the position reached; *n_alive = live candidates.
+template <int D, int RR>
+__device__ __forceinline__ u32 scan_steps(const uint4* sb, u32 j, u32 cnt, const DomSrc& src, const float4* pts,
+                                          CandsT<RR>& c, u32* n_alive) {
   constexpr int V = vec_of(D);
   constexpr int U = SCAN_U;
   // the staged block is padded with +inf images up to a multiple of U, so
   // the common path needs no bounds check (the rare FP32 path keeps one)
-  for (u32 j = 0; j < cnt; j += U) {
+  while (j < cnt) {
     uint4 w[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) w[u] = sb[j + u];
@@ -225,12 +280,12 @@ __device__ __forceinline__ void scan_smem(const uint4* sb, u32 cnt, const DomSrc
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int r = 0; r < R; ++r) hit |= codes_le<D>(w[u], c.c[r]);
+      for (int r = 0; r < RR; ++r) hit |= codes_le<D>(w[u], c.c[r]);
     if (hit) {
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
+        for (int r = 0; r < RR; ++r) {
           if (c.alive[r] && j + u < cnt && codes_le<D>(w[u], c.c[r])) {
             // for window dominators the FP32 copy may have been written in
             // an earlier round by another SM: read it through L2
@@ -249,13 +304,52 @@ __device__ __forceinline__ void scan_smem(const uint4* sb, u32 cnt, const DomSrc
           }
         }
     }
-    if ((j & 31) == 28) {
-      bool any = false;
-#pragma unroll
-      for (int r = 0; r < R; ++r) any |= c.alive[r];
-      if (!__any_sync(FULL, any)) break;
+    j += U;
+    if ((j & 31) == 0) {
+      const u32 n = alive_count(c);
+      if (n == 0 || (RR > 1 && n <= 32u * (RR / 2))) {
+        *n_alive = n;
+        return j;
+      }
     }
   }
+  *n_alive = alive_count(c);
+  return j;
+}
+
+// Scans the staged block sb[0..cnt) for the warp's candidates and records
+// their kills in `alive`.  Starts with R slots per lane and compacts the
+// live candidates into 2, then 1, slot as they die; sc/sp are the warp's
+// shared scratch (GS entries).
+template <int D>
+__device__ __forceinline__ void scan_smem(const uint4* sb, u32 cnt, const DomSrc& src, const float4* pts, Cands& c,
+                                          uint4* sc, u32* sp, u8* alive) {
+  static_assert(R == 4, "the compaction steps assume 4 slots per lane");
+  u32 n = alive_count(c);
+  u32 j = 0;
+  if (n > 64) {
+    j = scan_steps<D, 4>(sb, 0, cnt, src, pts, c, &n);
+    if (j >= cnt || n == 0) {
+      write_kills(c, alive);
+      return;
+    }
+  }
+  CandsT<1> c1;
+  if (n > 32) {
+    CandsT<2> c2;
+    compact(c, c2, sc, sp, alive);
+    j = scan_steps<D, 2>(sb, j, cnt, src, pts, c2, &n);
+    if (j >= cnt || n == 0) {
+      write_kills(c2, alive);
+      return;
+    }
+    compact(c2, c1, sc, sp, alive);
+  } else {
+    compact(c, c1, sc, sp, alive);
+    if (n == 0) return;
+  }
+  scan_steps<D, 1>(sb, j, cnt, src, pts, c1, &n);
+  write_kills(c1, alive);
 }
 
 __device__ __forceinline__ bool any_alive(const Cands& c) {
@@ -426,6 +520,8 @@ struct Meta {
 };
 
 struct Shared {
+  uint4 scode[WARPS][GS];  // per-warp compaction scratch of the scan
+  u32 spos[WARPS][GS];
   Meta meta[2];
   u64 bar[2];
   u32 bar_phase[2];
@@ -551,10 +647,7 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
     }
     if (__any_sync(FULL, any_alive(c))) {
       DomSrc src{sd.win, nullptr, 0};
-      scan_smem<D>(staged, cnt, src, sd.pts, c);
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (c.was[r] && !c.alive[r]) sd.alive[c.pos[r]] = 0;
+      scan_smem<D>(staged, cnt, src, sd.pts, c, S.scode[warp], S.spos[warp], sd.alive);
     }
   }
   __syncthreads();
@@ -717,10 +810,7 @@ __device__ void item_b(const Params& P, const SegDesc& sd, const Meta& mt, const
       load_cand<D>(sd, pos, valid, c, r);
     }
     if (__any_sync(FULL, any_alive(c))) {
-      scan_smem<D>(staged, cnt, src, sd.pts, c);
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (c.was[r] && !c.alive[r]) sd.alive[c.pos[r]] = 0;
+      scan_smem<D>(staged, cnt, src, sd.pts, c, S.scode[warp], S.spos[warp], sd.alive);
     }
   }
   __syncthreads();
