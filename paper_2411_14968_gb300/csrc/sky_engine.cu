@@ -161,6 +161,27 @@ __device__ __forceinline__ bool codes_le(const uint4& w, const uint4& t) {
   return le;
 }
 
+// Sign bits of t - w per FP16 half, ORed over the image words: bit 15 / 31
+// is clear iff every attribute of the low / high halves has w <= t.  The
+// subtraction's sign is exact: t - w rounds to a value of the sign of the
+// exact difference (a nonzero difference of two FP16 numbers is at least
+// the smallest subnormal, so it never rounds to zero), t - t is +0, the
+// images are finite and never -0, and overflow keeps the sign; a dead
+// candidate (-inf) or a padding dominator (+inf) gives -inf.
+__device__ __forceinline__ u32 hsub2_bits(u32 t, u32 w) {
+  u32 r;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(t), "r"(w));
+  return r;
+}
+template <int D>
+__device__ __forceinline__ u32 fail_bits(const uint4& w, const uint4& t) {
+  u32 x = hsub2_bits(t.x, w.x);
+  if (HW<D>::value > 1) x |= hsub2_bits(t.y, w.y);
+  if (HW<D>::value > 2) x |= hsub2_bits(t.z, w.z);
+  if (HW<D>::value > 3) x |= hsub2_bits(t.w, w.w);
+  return x;
+}
+
 // Def. 1 on the FP32 attributes.
 template <int D>
 __device__ __forceinline__ bool dominates_fp32(const float4* w, const float4* t) {
@@ -276,12 +297,18 @@ __device__ __forceinline__ u32 scan_steps(const uint4* sb, u32 j, u32 cnt, const
     uint4 w[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) w[u] = sb[j + u];
-    bool hit = false;
+    // fast rejection: bit 31 of acc stays set while every pair of the step
+    // fails in some attribute (bit 31 or 15 of its fail bits set); it
+    // clears for every pair that the exact FP16 test below would pass
+    u32 acc = 0xffffffffu;
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int r = 0; r < RR; ++r) hit |= codes_le<D>(w[u], c.c[r]);
-    if (hit) {
+      for (int r = 0; r < RR; ++r) {
+        const u32 x = fail_bits<D>(w[u], c.c[r]);
+        acc &= x | (x << 16);
+      }
+    if ((int)acc >= 0) {
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll

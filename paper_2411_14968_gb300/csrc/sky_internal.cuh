@@ -179,9 +179,11 @@ cudaError_t launch_compact_reps(const u8* rep_alive, const u32* excl, u32 nrep, 
 cudaError_t launch_stage_hist(const u8* stage_s, u64 n, u32* hist6, cudaStream_t st);
 
 // ---------------------------------------------------------------- dominance engine (sky_engine.cu)
-// FP16 images of a point's attributes: __float2half_rd of each attribute,
-// packed two per 32-bit word (attribute 2k in the low half), +0 padding.
-// Round-down is monotone, so w[a] > t[a] whenever code(w)[a] > code(t)[a].
+// FP16 images of a point's attributes: __float2half_rd of each attribute
+// clamped to [-65504, 65504], packed two per 32-bit word (attribute 2k in
+// the low half), +0 padding.  Both maps are monotone, so w[a] > t[a]
+// whenever code(w)[a] > code(t)[a]; images are finite and never -0 (the
+// attributes' -0.0 is turned into +0.0 first).
 //
 // One segment (a partition, or the whole merge input) of the SFS engine.
 // The points of a segment are sorted by score; win/whc and dpos/dhc have

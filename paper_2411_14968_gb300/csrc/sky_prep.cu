@@ -24,9 +24,12 @@ __device__ __forceinline__ float score_of(const float (&x)[8]) {
   return f;
 }
 
-// FP16 round-down images of the 8 (padded) attributes, two per word.
+// FP16 round-down images of the 8 (padded) attributes, two per word,
+// clamped to the finite FP16 range (clamping is monotone too, and keeps the
+// images finite, so differences of two images never produce NaN).
 __device__ __forceinline__ u32 pack_rd(float lo, float hi) {
-  __half a = __float2half_rd(lo), b = __float2half_rd(hi);
+  constexpr float HMAX = 65504.0f;
+  __half a = __float2half_rd(fminf(fmaxf(lo, -HMAX), HMAX)), b = __float2half_rd(fminf(fmaxf(hi, -HMAX), HMAX));
   return (u32)__half_as_ushort(a) | ((u32)__half_as_ushort(b) << 16);
 }
 __device__ __forceinline__ uint4 fp16_codes(const float (&x)[8]) {

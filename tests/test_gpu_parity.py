@@ -117,7 +117,9 @@ def test_fp16_image_collisions(ctx, oracle_mod):
     # The engine rejects pairs on FP16 round-down images before the FP32
     # test.  (a) every attribute in [1, 1 + 2^-10): all points share one FP16
     # image, so FP32 decides every test; (b) magnitudes beyond the FP16 range
-    # (round-down saturates at 65504 or goes to -inf) and negative values.
+    # (the images are clamped to +-65504) and negative values; (c) values of
+    # both signs around the FP16 subnormal range, where the images and their
+    # differences are subnormal or zero.
     rng = np.random.default_rng(12)
     n = 4000
     a = (1.0 + rng.integers(0, 512, (n, 4)) * 2.0 ** -23).astype(np.float32)
@@ -126,7 +128,10 @@ def test_fp16_image_collisions(ctx, oracle_mod):
     b[::11, 1] = np.float32(-3e38)
     b[::13, 4] = np.float32(70000.0)
     b[::17, 4] = np.float32(65504.0)
-    for x in (a, b):
+    c = (rng.standard_normal((n, 6)) * 2e-7).astype(np.float32)
+    c[::9, 3] = np.float32(5.96e-8)
+    c[::10, 0] = np.float32(-5.96e-8)
+    for x in (a, b, c):
         for scheme, p in (("none", 1), ("sliced", 4), ("random", 8)):
             _check(ctx, oracle_mod, x, scheme, p, rep="sorted", dom_block=128)
             _check(ctx, oracle_mod, x, scheme, p, merge="noseq")
