@@ -50,8 +50,10 @@
 // Dominance test.  Every point carries, next to its FP32 attributes, their
 // round-down FP16 images packed two per 32-bit word.  Round-down is monotone,
 // so if any FP16 image of w exceeds t's, then w exceeds t in that attribute
-// and cannot dominate t: the FP16 test rejects exactly, two attributes per
-// half2 compare, and only pairs it passes are tested in FP32 (Def. 1).
+// and cannot dominate t: the FP16 test (the signs of f16x2 differences, two
+// attributes per subtraction) rejects exactly, and only pairs it passes are
+// tested in FP32 (Def. 1).  A warp compacts its live candidates into fewer
+// slots per lane as they die, so dead lanes stop costing tests.
 //
 // Pipeline.  Thread 0 of a CTA claims the next item while the CTA scans the
 // current one and starts the bulk copy (cp.async.bulk, completing on an
@@ -61,7 +63,6 @@
 // dead.  Every wait (mbarrier, waiting for a ticket's task) is bounded: it
 // gives up with ERR_TIMEOUT when no item anywhere has completed for WAIT_NS.
 #include <algorithm>
-#include <cuda_fp16.h>
 #include "sky_internal.cuh"
 
 namespace sky {
@@ -139,6 +140,11 @@ __device__ bool mbar_wait(u64* bar, u32 parity, u32* err, u32* ctl) {
 }
 // Generic-proxy writes of global memory made visible to later bulk copies.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+// Orders this thread's earlier generic accesses of shared memory (the +inf
+// padding of a staging buffer) before a later bulk copy into it.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 
 // ------------------------------------------------------------ dominance test
 
@@ -146,20 +152,6 @@ template <int D>
 struct HW {
   static constexpr int value = (D + 1) / 2;  // half2 words that hold D attributes
 };
-
-__device__ __forceinline__ bool hle2(u32 a, u32 b) {
-  return __hble2(*reinterpret_cast<const __half2*>(&a), *reinterpret_cast<const __half2*>(&b));
-}
-
-// All FP16 images of w <= those of t (necessary for w to dominate t).
-template <int D>
-__device__ __forceinline__ bool codes_le(const uint4& w, const uint4& t) {
-  bool le = hle2(w.x, t.x);
-  if (HW<D>::value > 1) le &= hle2(w.y, t.y);
-  if (HW<D>::value > 2) le &= hle2(w.z, t.z);
-  if (HW<D>::value > 3) le &= hle2(w.w, t.w);
-  return le;
-}
 
 // Sign bits of t - w per FP16 half, ORed over the image words: bit 15 / 31
 // is clear iff every attribute of the low / high halves has w <= t.  The
@@ -180,6 +172,13 @@ __device__ __forceinline__ u32 fail_bits(const uint4& w, const uint4& t) {
   if (HW<D>::value > 2) x |= hsub2_bits(t.z, w.z);
   if (HW<D>::value > 3) x |= hsub2_bits(t.w, w.w);
   return x;
+}
+
+// All FP16 images of w <= those of t (necessary for w to dominate t), for
+// finite t and w.
+template <int D>
+__device__ __forceinline__ bool codes_le(const uint4& w, const uint4& t) {
+  return (fail_bits<D>(w, t) & 0x80008000u) == 0u;
 }
 
 // Def. 1 on the FP32 attributes.
@@ -628,6 +627,7 @@ __device__ void produce(const Params& P, Shared& S, int slot, uint4* buf) {
   m.copied = 0;
   if (m.cnt) {
     fence_proxy_async();
+    fence_proxy_async_smem();
     mbar_expect_tx(&S.bar[slot], m.cnt * 16u);
     bulk_g2s(buf, codes, m.cnt * 16u, &S.bar[slot]);
     m.copied = 1;
