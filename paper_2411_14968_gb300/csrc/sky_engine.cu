@@ -296,18 +296,19 @@ __device__ __forceinline__ u32 scan_steps(const uint4* sb, u32 j, u32 cnt, const
     uint4 w[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) w[u] = sb[j + u];
-    // fast rejection: bit 31 of acc stays set while every pair of the step
-    // fails in some attribute (bit 31 or 15 of its fail bits set); it
-    // clears for every pair that the exact FP16 test below would pass
+    // fast rejection, two pairs at a time: the high halves of the two fail
+    // words go to one word, the low halves to another, so bit 15 / 31 of
+    // their OR is set iff the first / second pair fails in some attribute;
+    // acc keeps both bits set while every pair of the step fails, and
+    // clears one for every pair that the exact FP16 test below would pass
     u32 acc = 0xffffffffu;
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int r = 0; r < RR; ++r) {
-        const u32 x = fail_bits<D>(w[u], c.c[r]);
-        acc &= x | (x << 16);
-      }
-    if ((int)acc >= 0) {
+    for (int q = 0; q < U * RR; q += 2) {
+      const u32 x0 = fail_bits<D>(w[q / RR], c.c[q % RR]);
+      const u32 x1 = fail_bits<D>(w[(q + 1) / RR], c.c[(q + 1) % RR]);
+      acc &= __byte_perm(x0, x1, 0x7632) | __byte_perm(x0, x1, 0x5410);
+    }
+    if ((acc & 0x80008000u) != 0x80008000u) {
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
