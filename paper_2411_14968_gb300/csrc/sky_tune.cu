@@ -15,7 +15,9 @@
 // tried with the others held at their best values so far; two sweeps,
 // within a trial budget.  Each candidate runs
 // twice and counts its faster run (the first may pay for growing the
-// workspace).
+// workspace); the winner is then confirmed against the starting knobs by the
+// median of five interleaved runs each.
+#include <algorithm>
 #include <cfloat>
 #include <cstring>
 #include <vector>
@@ -73,6 +75,7 @@ sky_status tune(sky_ctx* ctx, const sky_query* queries, uint32_t nq, uint32_t ma
   const int timing_was = sky::ctx_timing(ctx);
   sky_set_timing(ctx, 1);
   sky_params cur = *knobs;
+  sky_params start;
   if (!cur.dom_block) cur.dom_block = sky::DEFAULT_DOM_BLOCK;
   if (!cur.chunk_min) cur.chunk_min = sky::DEFAULT_CHUNK_MIN;
   if (!cur.chunk_max) cur.chunk_max = sky::DEFAULT_CHUNK_MAX;
@@ -85,25 +88,33 @@ sky_status tune(sky_ctx* ctx, const sky_query* queries, uint32_t nq, uint32_t ma
   };
   uint32_t trials = 0;
   sky_status status = SKY_OK;
-  auto measure = [&](const sky_params& k, double* ms) -> sky_status {
+  auto run_once = [&](const sky_params& k, double* ms) -> sky_status {
     for (uint32_t i = 0; i < nq; ++i) {
       ps[i].chunk_min = k.chunk_min;
       ps[i].chunk_max = k.chunk_max;
       ps[i].chunk_alpha_x4 = k.chunk_alpha_x4;
       ps[i].dom_block = k.dom_block;
     }
+    sky_status s = sky_skyline_batch(ctx, qs.data(), nq);
+    if (s != SKY_OK) return s;
+    sky_stats st;
+    sky_get_stats(ctx, &st);
+    *ms = st.ms_total;
+    return SKY_OK;
+  };
+  auto measure = [&](const sky_params& k, double* ms) -> sky_status {
     double best = DBL_MAX;
     for (int rep = 0; rep < 2; ++rep) {
-      sky_status s = sky_skyline_batch(ctx, qs.data(), nq);
+      double t = 0;
+      sky_status s = run_once(k, &t);
       if (s != SKY_OK) return s;
-      sky_stats st;
-      sky_get_stats(ctx, &st);
-      if (st.ms_total < best) best = st.ms_total;
+      if (t < best) best = t;
     }
     *ms = best;
     ++trials;
     return SKY_OK;
   };
+  start = cur;
   double cur_ms = 0;
   status = measure(cur, &cur_ms);
   // first a joint search over the two knobs that interact most (the chunk
@@ -142,6 +153,31 @@ sky_status tune(sky_ctx* ctx, const sky_query* queries, uint32_t nq, uint32_t ma
       }
     }
     if (!changed) break;
+  }
+  // The search compares the faster of two runs per candidate, and a batch's
+  // time varies from run to run (the work queue's order changes which
+  // dominators meet which candidates first), so a lucky run can pick a worse
+  // candidate.  Confirm the winner against the starting knobs with the
+  // median of CONFIRM interleaved runs each.
+  const bool moved = cur.chunk_min != start.chunk_min || cur.chunk_max != start.chunk_max ||
+                     cur.chunk_alpha_x4 != start.chunk_alpha_x4 || cur.dom_block != start.dom_block;
+  if (status == SKY_OK && moved) {
+    constexpr int CONFIRM = 5;
+    double a[CONFIRM], b[CONFIRM];
+    for (int i = 0; i < CONFIRM && status == SKY_OK; ++i) {
+      status = run_once(start, &a[i]);
+      if (status == SKY_OK) status = run_once(cur, &b[i]);
+    }
+    if (status == SKY_OK) {
+      std::sort(a, a + CONFIRM);
+      std::sort(b, b + CONFIRM);
+      if (a[CONFIRM / 2] <= b[CONFIRM / 2]) {
+        cur = start;
+        cur_ms = a[CONFIRM / 2];
+      } else {
+        cur_ms = b[CONFIRM / 2];
+      }
+    }
   }
   cudaFree(out);
   sky_set_timing(ctx, timing_was);
