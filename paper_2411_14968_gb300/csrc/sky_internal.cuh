@@ -86,14 +86,15 @@ cudaError_t scan_u32(const u32* in, u32* out, u64 n, bool exclusive, bool use_ma
 cudaError_t scan_u8(const u8* in, u32* out, u64 n, bool exclusive, u32* tmp, cudaStream_t st);
 
 // Stable LSD radix sort of (u64 key, u32 value) pairs on key bits [lo_bit,
-// hi_bit).  Input in k[0], v[0]; *out_sel receives the index (0 or 1) of the
-// buffer pair that holds the output.  hist: radix_hist_words(n) u32; tmp:
-// scan_tmp_words(radix_hist_words(n)) u32.  With n_dev the element count is
-// min(n, *n_dev), read on the device (n is the capacity the grids are sized
-// for), so no host round trip is needed.
-size_t radix_hist_words(u64 n);
-cudaError_t radix_sort(u64* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32* hist, u32* tmp,
-                       cudaStream_t st, int* out_sel, const u32* n_dev = nullptr);
+// hi_bit) (at most 64 bits, n < 2^32).  Input in k[0], v[0]; *out_sel
+// receives the index (0 or 1) of the buffer pair that holds the output.
+// work: radix_work_words(n) u32 (zeroed by the sort itself).  With n_dev the
+// element count is min(n, *n_dev), read on the device (n is the capacity the
+// grids are sized for), so no host round trip is needed.  err (optional)
+// receives ERR_TIMEOUT if a bounded look-back wait gave up.
+size_t radix_work_words(u64 n);
+cudaError_t radix_sort(u64* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32* work, cudaStream_t st,
+                       int* out_sel, const u32* n_dev = nullptr, u32* err = nullptr);
 
 // ---------------------------------------------------------------- prep (sky_prep.cu)
 struct PrepArgs {

@@ -141,9 +141,9 @@ size_t layout(const Plan& pl, u32 ang_words, Carve& c, Bufs* b) {
   b->alive = c.take<u8>(n);
   b->stage_s = c.take<u8>(n);
   b->seg_off = c.take<u32>(P + 1);
-  size_t scan_words = scan_tmp_words(std::max<u64>({(u64)radix_hist_words(n), n, P + 1, nrep}));
+  size_t scan_words = scan_tmp_words(std::max<u64>({n, (u64)P + 1, (u64)nrep}));
   b->scan_tmp = c.take<u32>(scan_words);
-  b->hist = c.take<u32>(radix_hist_words(n));
+  b->hist = c.take<u32>(radix_work_words(n));
   b->win = c.take<float>(n * 4 * V);
   b->whc = c.take<uint4>(n);
   b->dpos = c.take<u32>(n);
@@ -643,7 +643,7 @@ sky_status Runner::enqueue(BatchState& B) {
     CK(launch_prep(pr, D, st));
     int sel = 0;
     if (pl.scheme == SCHEME_RANDOM || pl.scheme == SCHEME_SLICED) {
-      CK(radix_sort(b.keys, b.vals, n, 0, 64, b.hist, b.scan_tmp, st, &sel));
+      CK(radix_sort(b.keys, b.vals, n, 0, 64, b.hist, st, &sel, nullptr, err));
       const u32* run_start = nullptr;
       if (pl.scheme == SCHEME_SLICED) {
         CK(launch_run_heads(b.keys[sel], n, b.head, st));
@@ -655,11 +655,11 @@ sky_status Runner::enqueue(BatchState& B) {
       u64* k2[2] = {b.keys[sel ^ 1], b.keys[sel]};
       u32* v2[2] = {b.vals[sel ^ 1], b.vals[sel]};
       int sel2 = 0;
-      CK(radix_sort(k2, v2, n, 0, 32 + pl.pid_bits, b.hist, b.scan_tmp, st, &sel2));
+      CK(radix_sort(k2, v2, n, 0, 32 + pl.pid_bits, b.hist, st, &sel2, nullptr, err));
       sel = sel2 == 0 ? (sel ^ 1) : sel;
     } else {
       int hi = (pl.scheme == SCHEME_NONE) ? 32 : 32 + pl.pid_bits;
-      CK(radix_sort(b.keys, b.vals, n, 0, hi, b.hist, b.scan_tmp, st, &sel));
+      CK(radix_sort(b.keys, b.vals, n, 0, hi, b.hist, st, &sel, nullptr, err));
     }
     GatherArgs ga{};
     ga.X = w.X;
@@ -799,7 +799,7 @@ sky_status Runner::enqueue(BatchState& B) {
     if (seq) {
       // sort u by score; |u| is read on the device
       int msel = 0;
-      CK(radix_sort(b.keys, b.vals, n, 0, 32, b.hist, b.scan_tmp, st, &msel, nu_dev));
+      CK(radix_sort(b.keys, b.vals, n, 0, 32, b.hist, st, &msel, nu_dev, b.words + W_ERR));
       CK(launch_gather_u(b.vals[msel], n, nu_dev, D, b.upts, b.uhc, b.uscore, b.upos, b.mpts, b.mhc, b.mscore,
                          b.mpos, st));
       CK(cudaMemsetAsync(b.malive, 1, n, st));

@@ -135,78 +135,173 @@ cudaError_t scan_impl(const In* in, u32* out, u64 n, bool exclusive, u32* tmp, c
 }
 
 // ---------------------------------------------------------------- radix sort
+//
+// Stable LSD radix sort with 8-bit digits, one kernel per digit (the
+// single-pass scheme with decoupled look-back of Adinets & Merrill,
+// "Onesweep", 2022): one kernel counts every digit of every pass up front,
+// one block scans those counts into global digit offsets, and each pass's
+// kernel then claims tiles in order, counts its tile's digits, publishes
+// them and looks back over the earlier tiles' published counts for its
+// offsets, and scatters its keys stably.
 
 constexpr int RT = 256;       // threads per block == radix buckets
 constexpr int RIPT = 16;      // keys per thread
 constexpr u64 RTILE = (u64)RT * RIPT;
+constexpr int MAX_PASS = 8;   // 64-bit keys
+constexpr u64 WAIT_NS_SORT = 2000000000ull;  // bound of a look-back wait without progress
+
+// Tile status word: bits 62..63 flag (1 = this tile's count, 2 = inclusive
+// count of tiles 0..this), bits 32..39 the pass (1-based, so a word from an
+// earlier pass of the same sort is not taken for this one), bits 0..31 the
+// count.  The status array is zeroed at the start of every sort.
+constexpr u64 ST_AGG = 1ull << 62, ST_INC = 2ull << 62;
+
+// Layout of the work buffer (u32 words): ghist[MAX_PASS][RT], tile counters
+// [MAX_PASS] (+ padding to 8 bytes), then the tile status words (u64).
+constexpr size_t W_GHIST = 0;
+constexpr size_t W_CTR = (size_t)MAX_PASS * RT;
+constexpr size_t W_STATUS = W_CTR + MAX_PASS + 8;  // even, so the u64 array is aligned
 
 // n_dev (optional): the element count lives in device memory and may be
-// below the capacity n the grid was sized for; blocks past it count nothing.
+// below the capacity n the grid was sized for; blocks past it do nothing.
 __device__ __forceinline__ u64 radix_count(u64 n, const u32* n_dev) {
   if (!n_dev) return n;
   u64 m = *n_dev;
   return m < n ? m : n;
 }
 
-__global__ void k_radix_hist(const u64* __restrict__ k, u64 n, const u32* __restrict__ n_dev, int shift, u32 mask,
-                             u32* __restrict__ hist, u32 nb) {
-  __shared__ u32 h[RT];
-  const int tid = threadIdx.x, lane = tid & 31;
-  n = radix_count(n, n_dev);
-  h[tid] = 0;
-  __syncthreads();
-  u64 base = (u64)blockIdx.x * RTILE;
-  for (int r = 0; r < RIPT; ++r) {
-    u64 e = base + (u64)r * RT + tid;
-    bool valid = e < n;
-    u32 dg = valid ? (u32)(k[e] >> shift) & mask : 0xffffffffu;
-    u32 peers = __match_any_sync(FULL, dg);
-    if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[dg], __popc(peers));
-  }
-  __syncthreads();
-  hist[(u64)tid * nb + blockIdx.x] = h[tid];
+__device__ __forceinline__ u64 sort_timer() {
+  u64 t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
-// Stable scatter: elements keep their input order inside each digit.
-__global__ void k_radix_scatter(const u64* __restrict__ kin, const u32* __restrict__ vin,
-                                u64* __restrict__ kout, u32* __restrict__ vout, u64 n,
-                                const u32* __restrict__ n_dev, int shift, u32 mask,
-                                const u32* __restrict__ offs, u32 nb) {
+// Counts the digits of every pass over one tile per block.
+__global__ void k_sort_hist(const u64* __restrict__ k, u64 n, const u32* __restrict__ n_dev, int lo_bit,
+                            int npass, int last_bits, u32* __restrict__ ghist) {
+  __shared__ u32 h[MAX_PASS][RT];
+  const int tid = threadIdx.x;
+  for (int p = 0; p < npass; ++p) h[p][tid] = 0;
+  __syncthreads();
+  n = radix_count(n, n_dev);
+  const u64 base = (u64)blockIdx.x * RTILE;
+  for (int r = 0; r < RIPT; ++r) {
+    const u64 e = base + (u64)r * RT + tid;
+    if (e >= n) break;
+    const u64 key = k[e];
+    for (int p = 0; p < npass; ++p) {
+      const u32 mask = p == npass - 1 ? (1u << last_bits) - 1u : 0xffu;
+      atomicAdd(&h[p][(u32)(key >> (lo_bit + 8 * p)) & mask], 1u);
+    }
+  }
+  __syncthreads();
+  for (int p = 0; p < npass; ++p)
+    if (h[p][tid]) atomicAdd(&ghist[(size_t)p * RT + tid], h[p][tid]);
+}
+
+// One block: exclusive scan of each pass's RT digit counts, in place.
+__global__ void k_sort_scan(u32* ghist, int npass) {
+  __shared__ u32 sh[32];
+  for (int p = 0; p < npass; ++p) {
+    u32* g = ghist + (size_t)p * RT;
+    const u32 v = g[threadIdx.x];
+    u32 agg;
+    const u32 inc = block_scan_incl(v, sh, &agg, OpAdd());
+    g[threadIdx.x] = inc - v;
+  }
+}
+
+// One digit pass.  Blocks claim tiles in order, so the tiles a block looks
+// back over are held by blocks that are running; a wait for one of them is
+// bounded anyway (error word, then the block carries on with what it saw).
+__global__ void k_sort_pass(const u64* __restrict__ kin, const u32* __restrict__ vin, u64* __restrict__ kout,
+                            u32* __restrict__ vout, u64 n, const u32* __restrict__ n_dev, int shift, u32 mask,
+                            const u32* __restrict__ gofs, u64* status, u32* tile_ctr, u32 pass_tag, u32* err) {
+  __shared__ u32 s_tile;
+  __shared__ u32 s_cnt[RT];
   __shared__ u32 s_base[RT];
   __shared__ u32 s_w[RT / 32][RT];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   n = radix_count(n, n_dev);
-  if ((u64)blockIdx.x * RTILE >= n) return;
-  s_base[tid] = offs[(u64)tid * nb + blockIdx.x];
+  if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  s_cnt[tid] = 0;
 #pragma unroll
   for (int w = 0; w < RT / 32; ++w) s_w[w][tid] = 0;
   __syncthreads();
-  u64 base = (u64)blockIdx.x * RTILE;
+  const u64 t = s_tile;
+  const u64 base = t * RTILE;
+  if (base >= n) return;
+  // this tile's digit counts
   for (int r = 0; r < RIPT; ++r) {
-    u64 e = base + (u64)r * RT + tid;
-    bool valid = e < n;
-    u64 key = valid ? kin[e] : 0;
-    u32 val = valid ? vin[e] : 0;
-    u32 dg = valid ? (u32)(key >> shift) & mask : 0xffffffffu;
-    u32 peers = __match_any_sync(FULL, dg);
-    u32 rank = __popc(peers & ((1u << lane) - 1u));
+    const u64 e = base + (u64)r * RT + tid;
+    const bool valid = e < n;
+    const u32 dg = valid ? (u32)(kin[e] >> shift) & mask : 0xffffffffu;
+    const u32 peers = __match_any_sync(FULL, dg);
+    if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[dg], __popc(peers));
+  }
+  __syncthreads();
+  // decoupled look-back, one digit per thread
+  {
+    const u32 c = s_cnt[tid];
+    volatile u64* st = status + t * RT + tid;
+    const u64 tag = (u64)pass_tag << 32;
+    u32 excl = 0;
+    if (t == 0) {
+      *st = ST_INC | tag | c;
+    } else {
+      *st = ST_AGG | tag | c;
+      u64 i = t - 1;
+      u64 t0 = 0;
+      for (;;) {
+        const u64 v = *(volatile const u64*)(status + i * RT + tid);
+        const bool ready = ((v >> 32) & 0xffu) == pass_tag && (v >> 62) != 0;
+        if (!ready) {
+          if (t0 == 0) {
+            t0 = sort_timer();
+          } else if (sort_timer() - t0 > WAIT_NS_SORT) {
+            if (err) atomicOr(err, ERR_TIMEOUT);
+            break;
+          }
+          continue;
+        }
+        t0 = 0;
+        excl += (u32)v;
+        if ((v & ST_INC) || i == 0) break;
+        --i;
+      }
+      *st = ST_INC | tag | (excl + c);
+    }
+    s_base[tid] = gofs[tid] + excl;
+  }
+  __syncthreads();
+  // stable scatter: keys keep their input order inside each digit
+  for (int r = 0; r < RIPT; ++r) {
+    const u64 e = base + (u64)r * RT + tid;
+    const bool valid = e < n;
+    const u64 key = valid ? kin[e] : 0;
+    const u32 val = valid ? vin[e] : 0;
+    const u32 dg = valid ? (u32)(key >> shift) & mask : 0xffffffffu;
+    const u32 peers = __match_any_sync(FULL, dg);
+    const u32 rank = __popc(peers & ((1u << lane) - 1u));
     if (valid && lane == __ffs(peers) - 1) s_w[warp][dg] = __popc(peers);
     __syncthreads();
     {
       u32 run = s_base[tid];
 #pragma unroll
       for (int w = 0; w < RT / 32; ++w) {
-        u32 c = s_w[w][tid];
+        const u32 cw = s_w[w][tid];
         s_w[w][tid] = run;
-        run += c;
+        run += cw;
       }
       s_base[tid] = run;
     }
     __syncthreads();
     if (valid) {
-      u32 pos = s_w[warp][dg] + rank;
-      kout[pos] = key;
-      vout[pos] = val;
+      const u32 pos = s_w[warp][dg] + rank;
+      if (pos < n) {  // always, unless a look-back wait gave up (then err is set)
+        kout[pos] = key;
+        vout[pos] = val;
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -230,26 +325,36 @@ cudaError_t scan_u8(const u8* in, u32* out, u64 n, bool exclusive, u32* tmp, cud
   return scan_impl<u8, OpAdd>(in, out, n, exclusive, tmp, st);
 }
 
-size_t radix_hist_words(u64 n) { return (size_t)RT * (size_t)((n + RTILE - 1) / RTILE) + 1; }
+size_t radix_work_words(u64 n) {
+  const u64 nb = (n + RTILE - 1) / RTILE;
+  return W_STATUS + 2 * (size_t)RT * (size_t)(nb ? nb : 1);
+}
 
-cudaError_t radix_sort(u64* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32* hist, u32* tmp,
-                       cudaStream_t st, int* out_sel, const u32* n_dev) {
+cudaError_t radix_sort(u64* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32* work, cudaStream_t st,
+                       int* out_sel, const u32* n_dev, u32* err) {
+  *out_sel = 0;
+  if (n <= 1 || hi_bit <= lo_bit) return cudaSuccess;
+  const int bits = hi_bit - lo_bit;
+  const int npass = (bits + 7) / 8;
+  if (npass > MAX_PASS || n >= (1ull << 32)) return cudaErrorInvalidValue;
+  const int last_bits = bits - 8 * (npass - 1);
+  const u64 nb = (n + RTILE - 1) / RTILE;
+  u32* ghist = work + W_GHIST;
+  u32* ctr = work + W_CTR;
+  u64* status = reinterpret_cast<u64*>(work + W_STATUS);
+  cudaError_t e = cudaMemsetAsync(work, 0, radix_work_words(n) * sizeof(u32), st);
+  if (e != cudaSuccess) return e;
+  note_launch();
+  k_sort_hist<<<(unsigned)nb, RT, 0, st>>>(k[0], n, n_dev, lo_bit, npass, last_bits, ghist);
+  note_launch();
+  k_sort_scan<<<1, RT, 0, st>>>(ghist, npass);
   int sel = 0;
-  u64 nb = (n + RTILE - 1) / RTILE;
-  if (n <= 1 || hi_bit <= lo_bit) {
-    *out_sel = 0;
-    return cudaSuccess;
-  }
-  for (int shift = lo_bit; shift < hi_bit; shift += 8) {
-    int bits = hi_bit - shift < 8 ? hi_bit - shift : 8;
-    u32 mask = (1u << bits) - 1u;
+  for (int p = 0; p < npass; ++p) {
+    const int shift = lo_bit + 8 * p;
+    const u32 mask = p == npass - 1 ? (1u << last_bits) - 1u : 0xffu;
     note_launch();
-    k_radix_hist<<<(unsigned)nb, RT, 0, st>>>(k[sel], n, n_dev, shift, mask, hist, (u32)nb);
-    cudaError_t e = scan_u32(hist, hist, (u64)RT * nb, true, false, tmp, st);
-    if (e != cudaSuccess) return e;
-    note_launch();
-    k_radix_scatter<<<(unsigned)nb, RT, 0, st>>>(k[sel], v[sel], k[sel ^ 1], v[sel ^ 1], n, n_dev, shift,
-                                                  mask, hist, (u32)nb);
+    k_sort_pass<<<(unsigned)nb, RT, 0, st>>>(k[sel], v[sel], k[sel ^ 1], v[sel ^ 1], n, n_dev, shift, mask,
+                                             ghist + (size_t)p * RT, status, ctr + p, (u32)(p + 1), err);
     sel ^= 1;
   }
   *out_sel = sel;
