@@ -165,20 +165,59 @@ __device__ __forceinline__ u32 hsub2_bits(u32 t, u32 w) {
   asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(t), "r"(w));
   return r;
 }
+// A candidate's images are kept duplicated, word k = (image k, image k); a
+// staged dominator pair is kept as word k = (image k of the first, image k
+// of the second).  One f16x2 subtraction per attribute then tests the
+// candidate against both dominators: bit 15 / 31 of the OR over the
+// attributes is clear iff every attribute of the first / second dominator
+// is <= the candidate's (the FP16 part of Def. 1's first condition).
 template <int D>
-__device__ __forceinline__ u32 fail_bits(const uint4& w, const uint4& t) {
-  u32 x = hsub2_bits(t.x, w.x);
-  if (HW<D>::value > 1) x |= hsub2_bits(t.y, w.y);
-  if (HW<D>::value > 2) x |= hsub2_bits(t.z, w.z);
-  if (HW<D>::value > 3) x |= hsub2_bits(t.w, w.w);
+__device__ __forceinline__ u32 pair_fail(const u32 (&t)[D], const u32 (&w)[D]) {
+  u32 x = hsub2_bits(t[0], w[0]);
+#pragma unroll
+  for (int k = 1; k < D; ++k) x |= hsub2_bits(t[k], w[k]);
   return x;
 }
 
-// All FP16 images of w <= those of t (necessary for w to dominate t), for
-// finite t and w.
+// Packed images (two attributes per word, attribute 2i in the low half) to
+// duplicated words and back.
 template <int D>
-__device__ __forceinline__ bool codes_le(const uint4& w, const uint4& t) {
-  return (fail_bits<D>(w, t) & 0x80008000u) == 0u;
+__device__ __forceinline__ void unpack_dup(const uint4& p, u32 (&t)[D]) {
+  const u32 w[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+  for (int k = 0; k < D; ++k) t[k] = __byte_perm(w[k / 2], 0u, (k & 1) ? 0x3232u : 0x1010u);
+}
+template <int D>
+__device__ __forceinline__ uint4 pack_dup(const u32 (&t)[D]) {
+  u32 w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const u32 lo = 2 * i < D ? t[2 * i] : 0u, hi = 2 * i + 1 < D ? t[2 * i + 1] : 0u;
+    w[i] = __byte_perm(lo, hi, 0x5410u);
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Rewrites a staged block of packed images in place as dominator pairs:
+// entries 2i and 2i+1 (two uint4) become pair i (two uint4, words 0..7 =
+// attributes 0..7 of both).  cnt4: the block's length rounded up to a
+// multiple of 4 (the +inf padding is converted too).  Every thread of the
+// CTA takes part; the caller synchronises.
+__device__ __forceinline__ void stage_pairs(uint4* sb, u32 cnt4, int tid, int nthreads) {
+  for (u32 i = tid; 2 * i < cnt4; i += nthreads) {
+    const uint4 a = sb[2 * i], b = sb[2 * i + 1];
+    uint4 lo, hi;
+    lo.x = __byte_perm(a.x, b.x, 0x5410u);
+    lo.y = __byte_perm(a.x, b.x, 0x7632u);
+    lo.z = __byte_perm(a.y, b.y, 0x5410u);
+    lo.w = __byte_perm(a.y, b.y, 0x7632u);
+    hi.x = __byte_perm(a.z, b.z, 0x5410u);
+    hi.y = __byte_perm(a.z, b.z, 0x7632u);
+    hi.z = __byte_perm(a.w, b.w, 0x5410u);
+    hi.w = __byte_perm(a.w, b.w, 0x7632u);
+    sb[2 * i] = lo;
+    sb[2 * i + 1] = hi;
+  }
 }
 
 // Def. 1 on the FP32 attributes.
@@ -207,14 +246,19 @@ constexpr u32 POS_INF2 = 0x7C007C00u;  // (+inf, +inf)
 
 // The candidates of one lane: RR slots (R when an item starts; fewer once
 // the warp's live candidates have been compacted).
-template <int RR>
+template <int D, int RR>
 struct CandsT {
-  uint4 c[RR];    // FP16 images (-inf when dead)
+  u32 t[RR][D];   // duplicated FP16 images (-inf when dead)
   u32 pos[RR];    // segment-relative position
   bool alive[RR];
   bool was[RR];
 };
-using Cands = CandsT<R>;
+
+template <int D>
+__device__ __forceinline__ void set_dead(u32 (&t)[D]) {
+#pragma unroll
+  for (int k = 0; k < D; ++k) t[k] = NEG_INF2;
+}
 
 // Where the FP32 attributes of dominator j of a staged block live: win[base
 // + j] (window) or pts[map[base + j]] (dense list).
@@ -232,8 +276,8 @@ __device__ __forceinline__ const float4* dom_fp32(const DomSrc& s, u32 j) {
   return s.fp32 + (u64)idx * V;
 }
 
-template <int RR>
-__device__ __forceinline__ u32 alive_count(const CandsT<RR>& c) {
+template <int D, int RR>
+__device__ __forceinline__ u32 alive_count(const CandsT<D, RR>& c) {
   u32 n = 0;
 #pragma unroll
   for (int r = 0; r < RR; ++r) n += __popc(__ballot_sync(FULL, c.alive[r]));
@@ -241,8 +285,8 @@ __device__ __forceinline__ u32 alive_count(const CandsT<RR>& c) {
 }
 
 // Records the warp's kills (candidates alive at load, dead now).
-template <int RR>
-__device__ __forceinline__ void write_kills(const CandsT<RR>& c, u8* alive) {
+template <int D, int RR>
+__device__ __forceinline__ void write_kills(const CandsT<D, RR>& c, u8* alive) {
 #pragma unroll
   for (int r = 0; r < RR; ++r)
     if (c.was[r] && !c.alive[r]) alive[c.pos[r]] = 0;
@@ -251,8 +295,8 @@ __device__ __forceinline__ void write_kills(const CandsT<RR>& c, u8* alive) {
 // Moves the warp's live candidates (at most 32 x RB of them) into RB slots
 // per lane, in slot-major order, through the warp's shared scratch; kills
 // are recorded first.
-template <int RA, int RB>
-__device__ __forceinline__ void compact(const CandsT<RA>& a, CandsT<RB>& b, uint4* sc, u32* sp, u8* alive) {
+template <int D, int RA, int RB>
+__device__ __forceinline__ void compact(const CandsT<D, RA>& a, CandsT<D, RB>& b, uint4* sc, u32* sp, u8* alive) {
   const int lane = threadIdx.x & 31;
   const u32 lt = (1u << lane) - 1u;
   write_kills(a, alive);
@@ -262,7 +306,7 @@ __device__ __forceinline__ void compact(const CandsT<RA>& a, CandsT<RB>& b, uint
     const u32 m = __ballot_sync(FULL, a.alive[r]);
     if (a.alive[r]) {
       const u32 k = k0 + __popc(m & lt);
-      sc[k] = a.c[r];
+      sc[k] = pack_dup<D>(a.t[r]);
       sp[k] = a.pos[r];
     }
     k0 += __popc(m);
@@ -274,64 +318,86 @@ __device__ __forceinline__ void compact(const CandsT<RA>& a, CandsT<RB>& b, uint
     const bool v = k < k0;
     b.alive[r] = v;
     b.was[r] = v;
-    b.c[r] = v ? sc[k] : make_uint4(NEG_INF2, NEG_INF2, NEG_INF2, NEG_INF2);
+    if (v) {
+      unpack_dup<D>(sc[k], b.t[r]);
+    } else {
+      set_dead<D>(b.t[r]);
+    }
     b.pos[r] = v ? sp[k] : 0u;
   }
   __syncwarp();
 }
 
-// Scans the staged block sb[j..cnt) for the warp's candidates, RR slots per
-// lane.  Every 32 dominators the warp counts its live candidates; it stops
-// early when none is left or when they fit in half the slots (the caller
-// compacts them and goes on with fewer slots, so dead lanes stop costing
-// compares).  Returns the position reached; *n_alive = live candidates.
+// Scans the staged block sb[j..cnt) (dominator pairs, see stage_pairs) for
+// the warp's candidates, RR slots per lane.  Every 32 dominators the warp
+// counts its live candidates; it stops early when none is left or when they
+// fit in half the slots (the caller compacts them and goes on with fewer
+// slots, so dead lanes stop costing compares).  Returns the position
+// reached; *n_alive = live candidates.
 template <int D, int RR>
 __device__ __forceinline__ u32 scan_steps(const uint4* sb, u32 j, u32 cnt, const DomSrc& src, const float4* pts,
-                                          CandsT<RR>& c, u32* n_alive) {
+                                          CandsT<D, RR>& c, u32* n_alive) {
   constexpr int V = vec_of(D);
-  constexpr int U = SCAN_U;
-  // the staged block is padded with +inf images up to a multiple of U, so
-  // the common path needs no bounds check (the rare FP32 path keeps one)
+  // dominator pairs per step (one for d > 6, which keeps the live registers
+  // of the widest images within the budget of two CTAs per SM)
+  constexpr int UP = D > 6 ? 1 : SCAN_U / 2;
+  // the staged block is padded with +inf images up to a multiple of
+  // SCAN_U, so the common path needs no bounds check (the rare FP32 path
+  // keeps one)
   while (j < cnt) {
-    uint4 w[U];
+    u32 w[UP][D];
 #pragma unroll
-    for (int u = 0; u < U; ++u) w[u] = sb[j + u];
-    // fast rejection, two pairs at a time: the high halves of the two fail
-    // words go to one word, the low halves to another, so bit 15 / 31 of
-    // their OR is set iff the first / second pair fails in some attribute;
-    // acc keeps both bits set while every pair of the step fails, and
-    // clears one for every pair that the exact FP16 test below would pass
+    for (int q = 0; q < UP; ++q) {
+      const uint4 a = sb[j + 2 * q];
+      w[q][0] = a.x;
+      if (D > 1) w[q][1 < D ? 1 : 0] = a.y;
+      if (D > 2) w[q][2 < D ? 2 : 0] = a.z;
+      if (D > 3) w[q][3 < D ? 3 : 0] = a.w;
+      if (D > 4) {
+        const uint4 b = sb[j + 2 * q + 1];
+        w[q][4 < D ? 4 : 0] = b.x;
+        if (D > 5) w[q][5 < D ? 5 : 0] = b.y;
+        if (D > 6) w[q][6 < D ? 6 : 0] = b.z;
+        if (D > 7) w[q][7 < D ? 7 : 0] = b.w;
+      }
+    }
+    // fast rejection: acc keeps bits 15 and 31 set while every candidate
+    // fails against both dominators of every pair of the step, and clears
+    // one for every (candidate, dominator) that the exact FP16 test passes
     u32 acc = 0xffffffffu;
 #pragma unroll
-    for (int q = 0; q < U * RR; q += 2) {
-      const u32 x0 = fail_bits<D>(w[q / RR], c.c[q % RR]);
-      const u32 x1 = fail_bits<D>(w[(q + 1) / RR], c.c[(q + 1) % RR]);
-      acc &= __byte_perm(x0, x1, 0x7632) | __byte_perm(x0, x1, 0x5410);
-    }
+    for (int q = 0; q < UP; ++q)
+#pragma unroll
+      for (int r = 0; r < RR; ++r) acc &= pair_fail<D>(c.t[r], w[q]);
     if ((acc & 0x80008000u) != 0x80008000u) {
 #pragma unroll
-      for (int u = 0; u < U; ++u)
+      for (int q = 0; q < UP; ++q)
 #pragma unroll
         for (int r = 0; r < RR; ++r) {
-          if (c.alive[r] && j + u < cnt && codes_le<D>(w[u], c.c[r])) {
-            // for window dominators the FP32 copy may have been written in
-            // an earlier round by another SM: read it through L2
-            const float4* wp = dom_fp32<D>(src, j + u);
-            float4 wv[2], tv[2];
-            wv[0] = __ldcg(wp);
-            tv[0] = __ldg(pts + (u64)c.pos[r] * V);
-            if (V > 1) {
-              wv[1] = __ldcg(wp + 1);
-              tv[1] = __ldg(pts + (u64)c.pos[r] * V + 1);
-            }
-            if (dominates_fp32<D>(wv, tv)) {
-              c.alive[r] = false;
-              c.c[r] = make_uint4(NEG_INF2, NEG_INF2, NEG_INF2, NEG_INF2);
+          const u32 x = pair_fail<D>(c.t[r], w[q]);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const u32 jd = j + 2 * q + h;
+            if (c.alive[r] && !((x >> (15 + 16 * h)) & 1u) && jd < cnt) {
+              // for window dominators the FP32 copy may have been written
+              // in an earlier round by another SM: read it through L2
+              const float4* wp = dom_fp32<D>(src, jd);
+              float4 wv[2], tv[2];
+              wv[0] = __ldcg(wp);
+              tv[0] = __ldg(pts + (u64)c.pos[r] * V);
+              if (V > 1) {
+                wv[1] = __ldcg(wp + 1);
+                tv[1] = __ldg(pts + (u64)c.pos[r] * V + 1);
+              }
+              if (dominates_fp32<D>(wv, tv)) {
+                c.alive[r] = false;
+                set_dead<D>(c.t[r]);
+              }
             }
           }
         }
     }
-    j += U;
+    j += 2 * UP;
     if ((j & 31) == 0) {
       const u32 n = alive_count(c);
       if (n == 0 || (RR > 1 && n <= 32u * (RR / 2))) {
@@ -349,7 +415,8 @@ __device__ __forceinline__ u32 scan_steps(const uint4* sb, u32 j, u32 cnt, const
 // live candidates into 2, then 1, slot as they die; sc/sp are the warp's
 // shared scratch (GS entries).
 template <int D>
-__device__ __forceinline__ void scan_smem(const uint4* sb, u32 cnt, const DomSrc& src, const float4* pts, Cands& c,
+__device__ __forceinline__ void scan_smem(const uint4* sb, u32 cnt, const DomSrc& src, const float4* pts,
+                                          CandsT<D, R>& c,
                                           uint4* sc, u32* sp, u8* alive) {
   static_assert(R == 4, "the compaction steps assume 4 slots per lane");
   u32 n = alive_count(c);
@@ -361,9 +428,9 @@ __device__ __forceinline__ void scan_smem(const uint4* sb, u32 cnt, const DomSrc
       return;
     }
   }
-  CandsT<1> c1;
+  CandsT<D, 1> c1;
   if (n > 32) {
-    CandsT<2> c2;
+    CandsT<D, 2> c2;
     compact(c, c2, sc, sp, alive);
     j = scan_steps<D, 2>(sb, j, cnt, src, pts, c2, &n);
     if (j >= cnt || n == 0) {
@@ -379,7 +446,8 @@ __device__ __forceinline__ void scan_smem(const uint4* sb, u32 cnt, const DomSrc
   write_kills(c1, alive);
 }
 
-__device__ __forceinline__ bool any_alive(const Cands& c) {
+template <int D>
+__device__ __forceinline__ bool any_alive(const CandsT<D, R>& c) {
   bool a = false;
 #pragma unroll
   for (int r = 0; r < R; ++r) a |= c.alive[r];
@@ -641,12 +709,16 @@ __device__ void produce(const Params& P, Shared& S, int slot, uint4* buf) {
 }
 
 template <int D>
-__device__ void load_cand(const SegDesc& sd, u32 pos, bool valid, Cands& c, int r) {
+__device__ void load_cand(const SegDesc& sd, u32 pos, bool valid, CandsT<D, R>& c, int r) {
   bool ok = valid && ld_cg_u8(sd.alive + pos);
   c.alive[r] = ok;
   c.was[r] = ok;
   c.pos[r] = pos;
-  c.c[r] = ok ? __ldg(sd.hc + pos) : make_uint4(NEG_INF2, NEG_INF2, NEG_INF2, NEG_INF2);
+  if (ok) {
+    unpack_dup<D>(__ldg(sd.hc + pos), c.t[r]);
+  } else {
+    set_dead<D>(c.t[r]);
+  }
 }
 
 // Phase A item: tile `tile` of the chunk against window block 0.
@@ -667,7 +739,7 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
   const u32 gbase = cs.cur + mt.tile * TILE + warp * GS;
 
   if (cnt) {
-    Cands c;
+    CandsT<D, R> c;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       u32 pos = gbase + r * 32 + lane;
@@ -829,7 +901,7 @@ __device__ void item_b(const Params& P, const SegDesc& sd, const Meta& mt, const
   const u32 cnt = mt.cnt;
   const DomSrc src = mt.dense ? DomSrc{sd.pts, sd.dpos, mt.base} : DomSrc{sd.win, nullptr, mt.base};
   if (cnt) {  // an item past the triangular bound has nothing to test
-    Cands c;
+    CandsT<D, R> c;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       u32 e = dbase + r * 32 + lane;
@@ -989,6 +1061,12 @@ __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
     const Meta m = S.meta[slot];
     if (m.state != M_READY) break;
     if (m.copied && !mbar_wait(&S.bar[slot], S.bar_phase[slot], P.err, P.ctl)) break;
+    if (m.copied) {
+      // dominator pairs for the scan; the proxy fence orders these generic
+      // writes before a later bulk copy into the same buffer
+      stage_pairs(cur_buf, (m.cnt + SCAN_U - 1) & ~(u32)(SCAN_U - 1), threadIdx.x, THREADS);
+      fence_proxy_async_smem();
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       if (m.copied) S.bar_phase[slot] ^= 1u;
