@@ -90,7 +90,7 @@ typedef struct {
   /* tuning knobs of the dominance engine; 0 selects the built-in default */
   uint32_t chunk_min;          /* smallest SFS chunk of a partition (points; default 1024) */
   uint32_t chunk_max;          /* largest SFS chunk of a partition (points; default 262144) */
-  uint32_t chunk_alpha_x4;     /* next chunk = alpha/4 x current window size, clamped (default 16) */
+  uint32_t chunk_alpha_x4;     /* next chunk = alpha/4 x current window size, clamped (default 32) */
   uint32_t dom_block;          /* dominator block per work item (points, multiple of 32, <= 2048; default 1024) */
 } sky_params;
 

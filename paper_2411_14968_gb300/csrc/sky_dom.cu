@@ -283,9 +283,12 @@ __global__ void k_build_segs(const u32* __restrict__ seg_off, u32 P, const u8* _
   sd.score = a.score + o;
   sd.alive = a.alive + o;
   sd.win = reinterpret_cast<float4*>(a.win) + (u64)o * V;
-  sd.whc = a.whc + o;
+  // image arrays of pairs: each segment starts at an even entry, with one
+  // entry of slack per segment (the arrays hold n + P + 2 entries)
+  const u64 q = ((u64)o + s + 1) & ~1ull;
+  sd.whc = a.whc + q;
   sd.dpos = a.dpos + o;
-  sd.dhc = a.dhc + o;
+  sd.dhc = a.dhc + q;
   sd.n = (dropped && dropped[s]) ? 0u : seg_off[s + 1] - o;
   sd.d = (u32)d;
   segs[s] = sd;

@@ -140,11 +140,7 @@ __device__ bool mbar_wait(u64* bar, u32 parity, u32* err, u32* ctl) {
 }
 // Generic-proxy writes of global memory made visible to later bulk copies.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
-// Orders this thread's earlier generic accesses of shared memory (the +inf
-// padding of a staging buffer) before a later bulk copy into it.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
+
 
 // ------------------------------------------------------------ dominance test
 
@@ -198,26 +194,17 @@ __device__ __forceinline__ uint4 pack_dup(const u32 (&t)[D]) {
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// Rewrites a staged block of packed images in place as dominator pairs:
-// entries 2i and 2i+1 (two uint4) become pair i (two uint4, words 0..7 =
-// attributes 0..7 of both).  cnt4: the block's length rounded up to a
-// multiple of 4 (the +inf padding is converted too).  Every thread of the
-// CTA takes part; the caller synchronises.
-__device__ __forceinline__ void stage_pairs(uint4* sb, u32 cnt4, int tid, int nthreads) {
-  for (u32 i = tid; 2 * i < cnt4; i += nthreads) {
-    const uint4 a = sb[2 * i], b = sb[2 * i + 1];
-    uint4 lo, hi;
-    lo.x = __byte_perm(a.x, b.x, 0x5410u);
-    lo.y = __byte_perm(a.x, b.x, 0x7632u);
-    lo.z = __byte_perm(a.y, b.y, 0x5410u);
-    lo.w = __byte_perm(a.y, b.y, 0x7632u);
-    hi.x = __byte_perm(a.z, b.z, 0x5410u);
-    hi.y = __byte_perm(a.z, b.z, 0x7632u);
-    hi.z = __byte_perm(a.w, b.w, 0x5410u);
-    hi.w = __byte_perm(a.w, b.w, 0x7632u);
-    sb[2 * i] = lo;
-    sb[2 * i + 1] = hi;
-  }
+// Window and dense-list images are stored as pairs: entries 2i and 2i+1
+// share 32 bytes (two uint4), word k = (image k of entry 2i, image k of
+// entry 2i+1), so a bulk copy of a block lands in shared memory as the
+// dominator pairs the scan tests.  Writes entry j's D images (two-byte
+// stores into its half of the pair's words).
+template <int D>
+__device__ __forceinline__ void put_pair_entry(uint4* arr, u32 j, const uint4& packed) {
+  unsigned short* h = reinterpret_cast<unsigned short*>(arr) + (size_t)(j >> 1) * 16 + (j & 1);
+  const u32 w[4] = {packed.x, packed.y, packed.z, packed.w};
+#pragma unroll
+  for (int k = 0; k < D; ++k) h[2 * k] = (unsigned short)((k & 1) ? (w[k / 2] >> 16) : (w[k / 2] & 0xffffu));
 }
 
 // Def. 1 on the FP32 attributes.
@@ -242,7 +229,6 @@ __device__ __forceinline__ bool dominates_fp32(const float4* w, const float4* t)
 
 constexpr int SCAN_U = 4;               // dominators per step of the scan loop
 constexpr u32 NEG_INF2 = 0xFC00FC00u;  // (-inf, -inf)
-constexpr u32 POS_INF2 = 0x7C007C00u;  // (+inf, +inf)
 
 // The candidates of one lane: RR slots (R when an item starts; fewer once
 // the warp's live candidates have been compacted).
@@ -328,7 +314,7 @@ __device__ __forceinline__ void compact(const CandsT<D, RA>& a, CandsT<D, RB>& b
   __syncwarp();
 }
 
-// Scans the staged block sb[j..cnt) (dominator pairs, see stage_pairs) for
+// Scans the staged block sb[j..cnt) (dominator pairs, see put_pair_entry) for
 // the warp's candidates, RR slots per lane.  Every 32 dominators the warp
 // counts its live candidates; it stops early when none is left or when they
 // fit in half the slots (the caller compacts them and goes on with fewer
@@ -341,9 +327,9 @@ __device__ __forceinline__ u32 scan_steps(const uint4* sb, u32 j, u32 cnt, const
   // dominator pairs per step (one for d > 6, which keeps the live registers
   // of the widest images within the budget of two CTAs per SM)
   constexpr int UP = D > 6 ? 1 : SCAN_U / 2;
-  // the staged block is padded with +inf images up to a multiple of
-  // SCAN_U, so the common path needs no bounds check (the rare FP32 path
-  // keeps one)
+  // the last step may read pairs past the block's end (whatever the
+  // buffer held): the FP32 path checks the bound, so a spurious pass there
+  // costs time only
   while (j < cnt) {
     u32 w[UP][D];
 #pragma unroll
@@ -695,15 +681,12 @@ __device__ void produce(const Params& P, Shared& S, int slot, uint4* buf) {
   }
   m.copied = 0;
   if (m.cnt) {
+    // whole pairs: m.base is even, the block is m.cnt entries rounded up
+    const u32 bytes = ((m.cnt + 1) & ~1u) * 16u;
     fence_proxy_async();
-    fence_proxy_async_smem();
-    mbar_expect_tx(&S.bar[slot], m.cnt * 16u);
-    bulk_g2s(buf, codes, m.cnt * 16u, &S.bar[slot]);
+    mbar_expect_tx(&S.bar[slot], bytes);
+    bulk_g2s(buf, codes, bytes, &S.bar[slot]);
     m.copied = 1;
-    // +inf padding up to a multiple of the scan step (beyond the copied
-    // range, so it does not race with the copy); read after the CTA barrier
-    // that follows the copy's completion
-    for (u32 i = m.cnt; i % SCAN_U; ++i) buf[i] = make_uint4(POS_INF2, POS_INF2, POS_INF2, POS_INF2);
   }
   m.state = M_READY;
 }
@@ -778,7 +761,7 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
       if (a) {
         u32 slot = base + __popc(m & ((1u << lane) - 1u));
         sd.dpos[slot] = pos;
-        sd.dhc[slot] = __ldg(sd.hc + pos);
+        put_pair_entry<D>(sd.dhc, slot, __ldg(sd.hc + pos));
       }
     }
   } else {
@@ -841,7 +824,7 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
         const u32 slot = off + __popc(bal[r] & lt);
         const u32 pos = gbase + r * 32 + lane;
         sd.dpos[slot] = pos;
-        sd.dhc[slot] = __ldg(sd.hc + pos);
+        put_pair_entry<D>(sd.dhc, slot, __ldg(sd.hc + pos));
       }
       off += __popc(bal[r]);
     }
@@ -939,7 +922,7 @@ __device__ void item_b(const Params& P, const SegDesc& sd, const Meta& mt, const
       float4* dst4 = sd.win + (u64)slot * V;
 #pragma unroll
       for (int v = 0; v < V; ++v) dst4[v] = __ldg(src4 + v);
-      sd.whc[slot] = __ldg(sd.hc + pos);
+      put_pair_entry<D>(sd.whc, slot, __ldg(sd.hc + pos));
     }
   }
   __threadfence();
@@ -1061,12 +1044,6 @@ __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
     const Meta m = S.meta[slot];
     if (m.state != M_READY) break;
     if (m.copied && !mbar_wait(&S.bar[slot], S.bar_phase[slot], P.err, P.ctl)) break;
-    if (m.copied) {
-      // dominator pairs for the scan; the proxy fence orders these generic
-      // writes before a later bulk copy into the same buffer
-      stage_pairs(cur_buf, (m.cnt + SCAN_U - 1) & ~(u32)(SCAN_U - 1), threadIdx.x, THREADS);
-      fence_proxy_async_smem();
-    }
     __syncthreads();
     if (threadIdx.x == 0) {
       if (m.copied) S.bar_phase[slot] ^= 1u;

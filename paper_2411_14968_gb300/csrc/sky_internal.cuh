@@ -188,16 +188,17 @@ cudaError_t launch_stage_hist(const u8* stage_s, u64 n, u32* hist6, cudaStream_t
 //
 // One segment (a partition, or the whole merge input) of the SFS engine.
 // The points of a segment are sorted by score; win/whc and dpos/dhc have
-// room for n entries each.
+// room for n entries each (whc and dhc for n + 1, rounded to whole pairs,
+// starting at an even entry of their arrays).
 struct SegDesc {
   const float4* pts;     // vec_of(d) float4 per point, sorted by score
   const uint4* hc;       // FP16 images of pts
   const float* score;
   u8* alive;
   float4* win;           // window: skyline points found so far (FP32)
-  uint4* whc;            // window FP16 images
+  uint4* whc;            // window FP16 images, stored as pairs (32 bytes per two entries)
   u32* dpos;             // dense list of the round: segment-relative positions
-  uint4* dhc;            // dense list FP16 images
+  uint4* dhc;            // dense list FP16 images, stored as pairs
   u32 n;
   u32 d;                 // attributes (1..8)
 };
@@ -216,10 +217,10 @@ struct SegState {
 };
 
 // Built-in defaults of the engine knobs (sky_params: 0 selects these).  A
-// short first chunk builds a window quickly; later chunks are 4x the window.
+// short first chunk builds a window quickly; later chunks are 8x the window.
 constexpr u32 DEFAULT_CHUNK_MIN = 1024;
 constexpr u32 DEFAULT_CHUNK_MAX = 262144;
-constexpr u32 DEFAULT_ALPHA_X4 = 16;
+constexpr u32 DEFAULT_ALPHA_X4 = 32;
 constexpr u32 DEFAULT_DOM_BLOCK = 1024;
 
 struct EngineCfg {

@@ -145,9 +145,9 @@ size_t layout(const Plan& pl, u32 ang_words, Carve& c, Bufs* b) {
   b->scan_tmp = c.take<u32>(scan_words);
   b->hist = c.take<u32>(radix_work_words(n));
   b->win = c.take<float>(n * 4 * V);
-  b->whc = c.take<uint4>(n);
+  b->whc = c.take<uint4>(n + P + 2);  // pairs: every partition starts at an even entry
   b->dpos = c.take<u32>(n);
-  b->dhc = c.take<uint4>(n);
+  b->dhc = c.take<uint4>(n + P + 2);
   b->upts = c.take<float>(n * 4 * V);
   b->uhc = c.take<uint4>(n);
   b->uscore = c.take<float>(n);

@@ -13,9 +13,8 @@
 // factor and the first chunk length (the two knobs that interact most),
 // then coordinate descent: for each knob in turn every candidate value is
 // tried with the others held at their best values so far; two sweeps,
-// within a trial budget.  Each candidate runs
-// twice and counts its faster run (the first may pay for growing the
-// workspace); the winner is then confirmed against the starting knobs by the
+// within a trial budget.  Each candidate runs three times and counts its
+// median run; the winner is then confirmed against the starting knobs by the
 // median of five interleaved runs each.
 #include <algorithm>
 #include <cfloat>
@@ -103,14 +102,13 @@ sky_status tune(sky_ctx* ctx, const sky_query* queries, uint32_t nq, uint32_t ma
     return SKY_OK;
   };
   auto measure = [&](const sky_params& k, double* ms) -> sky_status {
-    double best = DBL_MAX;
-    for (int rep = 0; rep < 2; ++rep) {
-      double t = 0;
-      sky_status s = run_once(k, &t);
+    double t[3];
+    for (int rep = 0; rep < 3; ++rep) {
+      sky_status s = run_once(k, &t[rep]);
       if (s != SKY_OK) return s;
-      if (t < best) best = t;
     }
-    *ms = best;
+    std::sort(t, t + 3);
+    *ms = t[1];
     ++trials;
     return SKY_OK;
   };
