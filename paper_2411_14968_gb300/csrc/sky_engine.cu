@@ -734,14 +734,18 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    u32 old = atomicAdd(P.tdoneA + mt.tgid, 1u);
-    S.flag = (old == per_tile - 1);
-    if (S.flag) P.tdoneA[mt.tgid] = 0;
+  // with one item per tile (always so while A_BLOCKS is 1) the item
+  // completes its tile and needs no completion counter
+  if (per_tile > 1) {
+    if (threadIdx.x == 0) {
+      __threadfence();
+      u32 old = atomicAdd(P.tdoneA + mt.tgid, 1u);
+      S.flag = (old == per_tile - 1);
+      if (S.flag) P.tdoneA[mt.tgid] = 0;
+    }
+    __syncthreads();
+    if (!S.flag) return;
   }
-  __syncthreads();
-  if (!S.flag) return;
   __threadfence();
   // The tile's flags are final for phase A: compact its survivors into the
   // dense list in position order.  The tile's offset is the sum of its
@@ -897,14 +901,16 @@ __device__ void item_b(const Params& P, const SegDesc& sd, const Meta& mt, const
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    u32 old = atomicAdd(P.tdoneB + mt.tgid, 1u);
-    S.flag = (old == per_tile - 1);
-    if (S.flag) P.tdoneB[mt.tgid] = 0;
+  if (per_tile > 1) {
+    if (threadIdx.x == 0) {
+      __threadfence();
+      u32 old = atomicAdd(P.tdoneB + mt.tgid, 1u);
+      S.flag = (old == per_tile - 1);
+      if (S.flag) P.tdoneB[mt.tgid] = 0;
+    }
+    __syncthreads();
+    if (!S.flag) return;
   }
-  __syncthreads();
-  if (!S.flag) return;
   __threadfence();
   // the dense tile's flags are final: append its survivors to the window
 #pragma unroll
