@@ -324,9 +324,11 @@ template <int D, int RR>
 __device__ __forceinline__ u32 scan_steps(const uint4* sb, u32 j, u32 cnt, const DomSrc& src, const float4* pts,
                                           CandsT<D, RR>& c, u32* n_alive) {
   constexpr int V = vec_of(D);
-  // dominator pairs per step (one for d > 6, which keeps the live registers
-  // of the widest images within the budget of two CTAs per SM)
-  constexpr int UP = D > 6 ? 1 : SCAN_U / 2;
+  // dominator pairs per step: more with fewer candidate slots (the step's
+  // fixed cost is spread over more tests), fewer for d > 6 (which keeps the
+  // live registers of the widest images within the budget of two CTAs per
+  // SM)
+  constexpr int UP = (D > 6 ? 1 : 2) * (RR == 1 ? 2 : 1);
   // the last step may read pairs past the block's end (whatever the
   // buffer held): the FP32 path checks the bound, so a spurious pass there
   // costs time only
