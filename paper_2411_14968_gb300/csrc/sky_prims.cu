@@ -214,35 +214,52 @@ __global__ void k_sort_scan(u32* ghist, int npass) {
 // One digit pass.  Blocks claim tiles in order, so the tiles a block looks
 // back over are held by blocks that are running; a wait for one of them is
 // bounded anyway (error word, then the block carries on with what it saw).
+// Warp w of a block owns the tile's keys [w * KPW, (w + 1) * KPW), lane-
+// strided, so the order (warp, iteration, lane) is the keys' input order:
+// each warp counts its digits in a private row, one scan across the rows
+// gives every warp its start per digit, and the warp then scatters its keys
+// in the same order, keeping them stable inside each digit.
+constexpr int KPW = RIPT * 32;  // keys per warp of a tile
+
 __global__ void k_sort_pass(const u64* __restrict__ kin, const u32* __restrict__ vin, u64* __restrict__ kout,
                             u32* __restrict__ vout, u64 n, const u32* __restrict__ n_dev, int shift, u32 mask,
                             const u32* __restrict__ gofs, u64* status, u32* tile_ctr, u32 pass_tag, u32* err) {
   __shared__ u32 s_tile;
-  __shared__ u32 s_cnt[RT];
   __shared__ u32 s_base[RT];
-  __shared__ u32 s_w[RT / 32][RT];
+  __shared__ u32 s_w[RT / 32][RT];  // per-warp digit counts, then per-warp digit starts
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const u32 lt = (1u << lane) - 1u;
   n = radix_count(n, n_dev);
   if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
-  s_cnt[tid] = 0;
 #pragma unroll
   for (int w = 0; w < RT / 32; ++w) s_w[w][tid] = 0;
   __syncthreads();
   const u64 t = s_tile;
   const u64 base = t * RTILE;
   if (base >= n) return;
-  // this tile's digit counts
+  const u64 wbase = base + (u64)warp * KPW;
+  // this warp's digit counts (a digit's leader lane adds its peers; leaders
+  // of one iteration hold distinct digits, so no atomics are needed)
   for (int r = 0; r < RIPT; ++r) {
-    const u64 e = base + (u64)r * RT + tid;
+    const u64 e = wbase + (u64)r * 32 + lane;
     const bool valid = e < n;
     const u32 dg = valid ? (u32)(kin[e] >> shift) & mask : 0xffffffffu;
     const u32 peers = __match_any_sync(FULL, dg);
-    if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[dg], __popc(peers));
+    if (valid && lane == __ffs(peers) - 1) s_w[warp][dg] += __popc(peers);
+    __syncwarp();
   }
   __syncthreads();
+  // per digit (one per thread): the tile's count, and each warp's start
+  // within the tile
+  u32 c = 0;
+#pragma unroll
+  for (int w = 0; w < RT / 32; ++w) {
+    const u32 cw = s_w[w][tid];
+    s_w[w][tid] = c;
+    c += cw;
+  }
   // decoupled look-back, one digit per thread
   {
-    const u32 c = s_cnt[tid];
     volatile u64* st = status + t * RT + tid;
     const u64 tag = (u64)pass_tag << 32;
     u32 excl = 0;
@@ -274,39 +291,23 @@ __global__ void k_sort_pass(const u64* __restrict__ kin, const u32* __restrict__
     s_base[tid] = gofs[tid] + excl;
   }
   __syncthreads();
-  // stable scatter: keys keep their input order inside each digit
+  // stable scatter, in the order of the count pass
   for (int r = 0; r < RIPT; ++r) {
-    const u64 e = base + (u64)r * RT + tid;
+    const u64 e = wbase + (u64)r * 32 + lane;
     const bool valid = e < n;
     const u64 key = valid ? kin[e] : 0;
     const u32 val = valid ? vin[e] : 0;
     const u32 dg = valid ? (u32)(key >> shift) & mask : 0xffffffffu;
     const u32 peers = __match_any_sync(FULL, dg);
-    const u32 rank = __popc(peers & ((1u << lane) - 1u));
-    if (valid && lane == __ffs(peers) - 1) s_w[warp][dg] = __popc(peers);
-    __syncthreads();
-    {
-      u32 run = s_base[tid];
-#pragma unroll
-      for (int w = 0; w < RT / 32; ++w) {
-        const u32 cw = s_w[w][tid];
-        s_w[w][tid] = run;
-        run += cw;
-      }
-      s_base[tid] = run;
+    u32 pos = 0;
+    if (valid) pos = s_base[dg] + s_w[warp][dg] + __popc(peers & lt);
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) s_w[warp][dg] += __popc(peers);
+    __syncwarp();
+    if (valid && pos < n) {  // always, unless a look-back wait gave up (then err is set)
+      kout[pos] = key;
+      vout[pos] = val;
     }
-    __syncthreads();
-    if (valid) {
-      const u32 pos = s_w[warp][dg] + rank;
-      if (pos < n) {  // always, unless a look-back wait gave up (then err is set)
-        kout[pos] = key;
-        vout[pos] = val;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int w = 0; w < RT / 32; ++w) s_w[w][tid] = 0;
-    __syncthreads();
   }
 }
 
