@@ -50,10 +50,12 @@
 // Dominance test.  Every point carries, next to its FP32 attributes, their
 // round-down FP16 images packed two per 32-bit word.  Round-down is monotone,
 // so if any FP16 image of w exceeds t's, then w exceeds t in that attribute
-// and cannot dominate t: the FP16 test (the signs of f16x2 differences, two
-// attributes per subtraction) rejects exactly, and only pairs it passes are
-// tested in FP32 (Def. 1).  A warp compacts its live candidates into fewer
-// slots per lane as they die, so dead lanes stop costing tests.
+// and cannot dominate t: the FP16 test (the signs of f16x2 differences; a
+// candidate's images are duplicated per word and staged dominators come in
+// pairs, so one subtraction tests one attribute of two pairs) rejects
+// exactly, and only pairs it passes are tested in FP32 (Def. 1).  A warp
+// compacts its live candidates into fewer slots per lane as they die, so
+// dead lanes stop costing tests.
 //
 // Pipeline.  Thread 0 of a CTA claims the next item while the CTA scans the
 // current one and starts the bulk copy (cp.async.bulk, completing on an
@@ -231,7 +233,10 @@ __device__ __forceinline__ bool dominates_fp32(const float4* w, const float4* t)
   return le && ne;
 }
 
-constexpr int SCAN_U = 4;               // dominators per step of the scan loop
+// Staging buffer entries beyond dom_block: a scan step may read past a
+// block's last entry up to the next multiple of 8 (blocks hold at most
+// dom_block entries, a multiple of 32).
+constexpr u32 STAGE_PAD = 4;
 constexpr u32 NEG_INF2 = 0xFC00FC00u;  // (-inf, -inf)
 
 // The candidates of one lane: RR slots (R when an item starts; fewer once
@@ -330,7 +335,7 @@ __device__ __forceinline__ u32 scan_steps(const uint4* sb, u32 j, u32 cnt, const
   constexpr int V = vec_of(D);
   // dominator pairs per step: more with fewer candidate slots (the step's
   // fixed cost is spread over more tests), fewer for d > 6 (which keeps the
-  // live registers of the widest images within the budget of two CTAs per
+  // live registers of the widest images within the budget of four CTAs per
   // SM)
   constexpr int UP = (D > 6 ? 1 : 2) * (RR == 1 ? 2 : 1);
   // the last step may read pairs past the block's end (whatever the
@@ -1012,7 +1017,7 @@ __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
   __shared__ Shared S;
   const u32 DB = P.cfg.dom_block;
   uint4* const buf0 = reinterpret_cast<uint4*>(dyn);  // two buffers of DB (+ padding) FP16 images
-  const u32 BUFN = DB + SCAN_U;
+  const u32 BUFN = DB + STAGE_PAD;
 
   if (threadIdx.x == 0) {
     mbar_init(&S.bar[0]);
@@ -1115,7 +1120,7 @@ cudaError_t engine_run(const SegDesc* segs_dev, u32 nseg, const EngineCfg& cfg, 
   P.task_cap = (u32)w.task_cap;
   P.ctl = w.ctl;
   P.err = err;
-  size_t smem = 2 * ((size_t)cfg.dom_block + SCAN_U) * sizeof(uint4);
+  size_t smem = 2 * ((size_t)cfg.dom_block + STAGE_PAD) * sizeof(uint4);
   cudaError_t e = cudaFuncSetAttribute(k_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
