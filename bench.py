@@ -136,9 +136,11 @@ def load_workcounts():
         return json.load(fh)["variants"]
 
 
-def cpu_oracle_sample(n_sample: int):
-    """Times the CPU oracle (single-threaded C, as it stands) on the same
-    variants over the first n_sample points of the same generator."""
+def cpu_oracle_sample(n_sample: int, threads: int = 1):
+    """Times the CPU oracle (C, as it stands) on the same variants over the
+    first n_sample points of the same generator.  threads > 1 spreads
+    Algorithm 2's local skylines over that many OpenMP threads (the merge
+    stays sequential, as in the paper)."""
     from oracle import oracle as O
     from paper_2411_14968_gb300 import datagen
     x = datagen.anticorrelated(n_sample, D, SEED)
@@ -149,10 +151,14 @@ def cpu_oracle_sample(n_sample: int):
         "angular_rep": dict(scheme=O.ANGULAR, slices=[4, 2, 2, 2, 2], rep=O.REP_SORTED),
     }
     O.build()
-    t = time.perf_counter()
-    for name, _ in VARIANTS:
-        O.partitioned(x, **kw[name])
-    return time.perf_counter() - t, len(VARIANTS) * n_sample
+    O.set_threads(threads)
+    try:
+        t = time.perf_counter()
+        for name, _ in VARIANTS:
+            O.partitioned(x, **kw[name])
+        return time.perf_counter() - t, len(VARIANTS) * n_sample
+    finally:
+        O.set_threads(1)
 
 
 def reference_arm(args, rank, world):
@@ -458,6 +464,14 @@ def gpu_arm(args, rank, world, local):
         secs, pts = cpu_oracle_sample(n_sample)
         cpu = {"value": pts / secs, "unit": "points/s", "cores": 1, "kind": "oracle",
                "sample": f"first {n_sample} points of the same generator, the 4 variants once ({secs:.1f} s)"}
+        from oracle import oracle as O
+        threads = min(O.max_threads(), os.cpu_count() or 1)
+        if threads > 1:
+            secs_mt, pts_mt = cpu_oracle_sample(n_sample, threads)
+            cpu["parallel"] = {
+                "value": pts_mt / secs_mt, "unit": "points/s", "cores": threads,
+                "kind": "oracle with Algorithm 2's local skylines over OpenMP threads (sequential merge)",
+                "sample": f"the same sample ({secs_mt:.1f} s)"}
 
     if rank == 0:
         line = {

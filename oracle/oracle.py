@@ -43,9 +43,12 @@ def build(force: bool = False) -> str:
         os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
     if force or stale:
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call([
-            "gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-            "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+        # OpenMP only serves the multi-threaded CPU timing; without it the
+        # oracle is built single-threaded
+        r = subprocess.run(base + ["-fopenmp", "-o", tmp, _SRC, "-lm"], capture_output=True)
+        if r.returncode != 0:
+            subprocess.check_call(base + ["-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -78,6 +81,8 @@ def _load():
         lib.orc_partitioned.argtypes = [P, i64, i32, i32, u32, P, i32, i32, u64,
                                         i32, i32, u32, i32, P, P, P]
         lib.orc_partitioned.restype = i64
+        lib.orc_set_threads.argtypes = [i32]
+        lib.orc_max_threads.restype = i32
         _lib = lib
         return lib
 
@@ -208,6 +213,17 @@ def grid_filter(pid, d: int, slices) -> np.ndarray:
     out = np.zeros(P, dtype=np.uint8)
     _load().orc_grid_filter(_ptr(pid), pid.shape[0], d, _ptr(m), _ptr(out))
     return out.astype(bool)
+
+
+def set_threads(n: int) -> None:
+    """Threads for Algorithm 2's parallel loops (local skylines, NoSeq checks);
+    1 (the default) runs the plain single-threaded loops."""
+    _load().orc_set_threads(int(n))
+
+
+def max_threads() -> int:
+    """Threads OpenMP offers (1 when the oracle was built without it)."""
+    return int(_load().orc_max_threads())
 
 
 def partitioned(points, scheme: int = NONE, p: int = 1, slices=None, normalize: bool = False,

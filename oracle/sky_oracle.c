@@ -6,8 +6,12 @@
  * leg of the benchmark may load this library.  The GPU library never links,
  * includes or calls it, and this file includes nothing from the GPU library.
  *
- * Everything here is deliberately slow and direct: single-threaded loops written
- * from the paper's definitions, no blocking, no fusion.  Floating point is the
+ * Everything here is deliberately slow and direct: loops written from the
+ * paper's definitions, no blocking, no fusion.  They run single-threaded unless
+ * orc_set_threads asks for more: then Algorithm 2's two parallel loops (the
+ * local skyline of every partition, and NoSeq's per-tuple checks) are spread
+ * over OpenMP threads, as the paper spreads them over cores; results and test
+ * counts are the same for any thread count.  Floating point is the
  * input's own FP32 (the method compares the caller's FP32 values), compiled
  * with -ffp-contract=off and without fast-math so every sum is a correctly
  * rounded FP32 addition in the stated order.
@@ -41,6 +45,9 @@
  *    Sliced the u_j with j < i.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -105,12 +112,29 @@ void orc_scores(const float *pts, int64_t n, int d, float *out) {
   for (int64_t i = 0; i < n; ++i) out[i] = score_of(pts + i * d, d);
 }
 
+/* ------------------------------------------------------------ threads */
+
+/* Threads of Algorithm 2's parallel loops (1: the plain loops).  Only the
+   CPU timing of the method uses more than one. */
+static int g_threads = 1;
+
+void orc_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+
+/* Threads available to the parallel loops (1 when built without OpenMP). */
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 /* ------------------------------------------------------------ Algorithm 1 (SFS) */
 
 typedef struct { float f; int64_t id; } scored_t;
 
-static const float *g_pts; /* single-threaded oracle: sort context */
-static int g_d;
+static _Thread_local const float *g_pts; /* sort context of the calling thread */
+static _Thread_local int g_d;
 
 /* (f, x_1..x_d, id) ascending: a linear extension of dominance (if s dominates
    t then f(s) <= f(t) and, on equal f, s precedes t lexicographically). */
@@ -487,13 +511,16 @@ int64_t orc_partitioned(const float *pts, int64_t n, int d, int scheme, uint32_t
   uint8_t *flag = (uint8_t *)calloc((size_t)n, 1);
   int64_t *sub = (int64_t *)malloc((size_t)n * sizeof(int64_t));
   uint64_t t_local = 0, t_merge = 0;
-  for (uint64_t q = 0; q < P; ++q) {
+  /* the partitions are independent: each uses its own slice of sub */
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 1) reduction(+ : t_local) if (g_threads > 1)
+  for (int64_t q = 0; q < (int64_t)P; ++q) {
+    int64_t *own = sub + cnt[q];
     int64_t m = 0;
     for (int64_t j = cnt[q]; j < cnt[q + 1]; ++j)
-      if (!stage[mem[j]]) sub[m++] = mem[j];
-    orc_sfs(pts, d, sub, m, flag, &t_local);
+      if (!stage[mem[j]]) own[m++] = mem[j];
+    orc_sfs(pts, d, own, m, flag, &t_local);
     for (int64_t j = 0; j < m; ++j)
-      if (!flag[sub[j]]) stage[sub[j]] = ORC_ST_LOCAL;
+      if (!flag[own[j]]) stage[own[j]] = ORC_ST_LOCAL;
   }
 
   /* final phase: Sky(u) (sequential) or the NoSeq identity of Prop. 2 */
@@ -510,9 +537,11 @@ int64_t orc_partitioned(const float *pts, int64_t n, int d, int scheme, uint32_t
       result += flag[i];
     }
   } else {
-    uint32_t ci[8], cj[8];
     uint8_t *kill = (uint8_t *)calloc((size_t)n, 1);
+    /* every union tuple is checked independently */
+#pragma omp parallel for num_threads(g_threads) schedule(dynamic, 64) reduction(+ : t_merge) if (g_threads > 1)
     for (int64_t a = 0; a < nu; ++a) {
+      uint32_t ci[8], cj[8];
       int64_t t = sub[a];
       uint32_t pi = pid[t];
       if (scheme == ORC_GRID) cell_coords(pi, d, slices, ci);

@@ -340,6 +340,28 @@ def test_partitioned_equals_skyline(oracle_mod, kind, d):
                     assert not oracle_mod.relative_skyline(x[i:i + 1], mates)[0]
 
 
+def test_threaded_loops_change_nothing(oracle_mod):
+    """Algorithm 2's local skylines and NoSeq's checks are independent per
+    partition / per tuple: with several threads the index set, partitions,
+    stage codes and dominance-test counts are those of the plain loops."""
+    x = datagen.anticorrelated(6000, 5, 3)
+    cases = [dict(scheme=oracle_mod.SLICED, p=37), dict(scheme=oracle_mod.RANDOM, p=16, seed=3),
+             dict(scheme=oracle_mod.GRID, slices=[2] * 5), dict(scheme=oracle_mod.ANGULAR, slices=[3, 2, 2, 2])]
+    try:
+        for kw in cases:
+            for rep in (0, 1):
+                for merge in (0, 1):
+                    oracle_mod.set_threads(1)
+                    a = oracle_mod.partitioned(x, rep=rep, merge=merge, **kw)
+                    oracle_mod.set_threads(4)
+                    b = oracle_mod.partitioned(x, rep=rep, merge=merge, **kw)
+                    for key in ("indices", "pid", "stage"):
+                        np.testing.assert_array_equal(a[key], b[key], err_msg=f"{kw} {key}")
+                    assert a["tests"] == b["tests"]
+    finally:
+        oracle_mod.set_threads(1)
+
+
 def test_partitioned_edge_cases(oracle_mod):
     for n in (0, 1, 2, 3):
         x = datagen.independent(n, 3, 1)
