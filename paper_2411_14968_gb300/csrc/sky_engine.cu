@@ -608,6 +608,7 @@ struct Meta {
   u32 base;    // index of the first staged dominator in its source
   u32 dense;   // 1: the dominators are dense-list points (FP32 via dpos)
   u32 copied;  // 1: a bulk copy into the item's buffer was issued
+  u32 counted; // 1: the producer counted the item towards its tile (empty item completing the tile)
 };
 
 struct Shared {
@@ -627,17 +628,26 @@ struct Shared {
 // and including the tile.
 constexpr u32 TS_AGG = 1u << 30, TS_INC = 2u << 30, TS_VAL = TS_AGG - 1;
 
+// Empty items (dense blocks past a tile's triangular bound) the producer may
+// retire in one call before it hands the CTA a ticket still pending.
+constexpr int SKIP_MAX = 32;
+
 // Producer (thread 0 only, never blocks): claims a ticket for buffer `slot`
 // if it has none, and once the ticket's task is known plans the item and
 // starts the bulk copy of its dominator block's FP16 images.  The buffer is
-// free: every warp has finished the item that used it.
+// free: every warp has finished the item that used it.  A phase-B item whose
+// dense block lies past its tile's triangular bound tests nothing: the
+// producer counts it towards its tile's completion itself and claims the
+// next ticket, unless the item is the one that completes the tile (then the
+// CTA runs it, already counted, to append the tile's survivors).
 __device__ void produce(const Params& P, Shared& S, int slot, uint4* buf) {
   Meta& m = S.meta[slot];
+  for (int skips = 0;; ++skips) {
   if (m.state == M_EMPTY) {
     m.ticket = atomicAdd(P.ctl + C_TICKET, 1u);
     m.state = M_PENDING;
   }
-  if (m.state != M_PENDING) return;
+  if (m.state != M_PENDING || skips == SKIP_MAX) return;
   u32 idx = 0;
   const int f = find_task(P, m.ticket, &S.cursor, &idx);
   if (f < 0) {
@@ -645,6 +655,7 @@ __device__ void produce(const Params& P, Shared& S, int slot, uint4* buf) {
     return;
   }
   if (f == 0) return;
+  m.counted = 0;
   const Task* tk = P.tasks + idx;
   const u32 DB = P.cfg.dom_block;
   m.s = __ldcg(&tk->s);
@@ -687,6 +698,17 @@ __device__ void produce(const Params& P, Shared& S, int slot, uint4* buf) {
       m.cnt = m.base < e ? min(DB, e - m.base) : 0;
       m.dense = 1;
       codes = sd->dhc + m.base;
+      const u32 per_tile = wbB + ceil_div(dlen, DB);
+      if (m.cnt == 0 && per_tile > 1) {
+        // nothing to test (no kills to publish, so no fence before the count)
+        const u32 old = atomicAdd(P.tdoneB + m.tgid, 1u);
+        if (old != per_tile - 1) {
+          m.state = M_EMPTY;
+          continue;
+        }
+        P.tdoneB[m.tgid] = 0;
+        m.counted = 1;
+      }
     }
   }
   m.copied = 0;
@@ -699,6 +721,8 @@ __device__ void produce(const Params& P, Shared& S, int slot, uint4* buf) {
     m.copied = 1;
   }
   m.state = M_READY;
+  return;
+  }
 }
 
 template <int D>
@@ -913,10 +937,14 @@ __device__ void item_b(const Params& P, const SegDesc& sd, const Meta& mt, const
   __syncthreads();
   if (per_tile > 1) {
     if (threadIdx.x == 0) {
-      __threadfence();
-      u32 old = atomicAdd(P.tdoneB + mt.tgid, 1u);
-      S.flag = (old == per_tile - 1);
-      if (S.flag) P.tdoneB[mt.tgid] = 0;
+      if (mt.counted) {
+        S.flag = 1;
+      } else {
+        __threadfence();
+        u32 old = atomicAdd(P.tdoneB + mt.tgid, 1u);
+        S.flag = (old == per_tile - 1);
+        if (S.flag) P.tdoneB[mt.tgid] = 0;
+      }
     }
     __syncthreads();
     if (!S.flag) return;
