@@ -57,10 +57,11 @@
 // compacts its live candidates into fewer slots per lane as they die, so
 // dead lanes stop costing tests.
 //
-// Pipeline.  Thread 0 of a CTA claims the next item while the CTA scans the
-// current one and starts the bulk copy (cp.async.bulk, completing on an
-// mbarrier) of the next item's dominator block into the second of two
-// shared-memory buffers; each warp scans the staged block with broadcast
+// Pipeline.  The first warp to finish its part of the current item claims
+// the next item (while the other warps still scan) and starts the bulk copy
+// (cp.async.bulk, completing on an mbarrier) of the next item's dominator
+// block into the second of two shared-memory buffers; each warp scans the
+// staged block with broadcast
 // shared loads and leaves the item when a ballot shows all its candidates
 // dead.  Every wait (mbarrier, waiting for a ticket's task) is bounded: it
 // gives up with ERR_TIMEOUT when no item anywhere has completed for WAIT_NS.
@@ -621,6 +622,9 @@ struct Shared {
   u32 flag;
   u32 wtot[WARPS];
   u32 tile_base;
+  u32 pclaim;   // warps past their scan of the current item (the first one produces)
+  int pslot;    // buffer slot of the next item
+  uint4* pbuf;  // and its buffer
 };
 
 // Tile status words of the ordered compaction (decoupled look-back): the
@@ -725,6 +729,14 @@ __device__ void produce(const Params& P, Shared& S, int slot, uint4* buf) {
   }
 }
 
+// The first warp to finish its scan of the current item plans the next one
+// (produce), so the producer's memory round trips delay no warp that still
+// has candidates to test.
+__device__ __forceinline__ void produce_next(const Params& P, Shared& S) {
+  if ((threadIdx.x & 31) == 0 && atomicAdd(&S.pclaim, 1u) == 0) produce(P, S, S.pslot, S.pbuf);
+  __syncwarp();
+}
+
 template <int D>
 __device__ void load_cand(const SegDesc& sd, u32 pos, bool valid, CandsT<D, R>& c, int r) {
   bool ok = valid && ld_cg_u8(sd.alive + pos);
@@ -767,6 +779,7 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
       scan_smem<D>(staged, cnt, src, sd.pts, c, S.scode[warp], S.spos[warp], sd.alive);
     }
   }
+  produce_next(P, S);
   __syncthreads();
   // with one item per tile (always so while A_BLOCKS is 1) the item
   // completes its tile and needs no completion counter
@@ -934,6 +947,7 @@ __device__ void item_b(const Params& P, const SegDesc& sd, const Meta& mt, const
       scan_smem<D>(staged, cnt, src, sd.pts, c, S.scode[warp], S.spos[warp], sd.alive);
     }
   }
+  produce_next(P, S);
   __syncthreads();
   if (per_tile > 1) {
     if (threadIdx.x == 0) {
@@ -1063,6 +1077,10 @@ __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
     uint4* const cur_buf = buf0 + (size_t)slot * BUFN;
     // wait until the slot's ticket has a task (or there is no more work)
     if (threadIdx.x == 0) {
+      // every warp has left the previous item (and its producer call)
+      S.pclaim = 0;
+      S.pslot = slot ^ 1;
+      S.pbuf = buf0 + (size_t)(slot ^ 1) * BUFN;
       u64 t0 = 0;
       u32 seen = 0;
       while (S.meta[slot].state == M_PENDING) {
@@ -1092,7 +1110,6 @@ __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
     if (threadIdx.x == 0) {
       if (m.copied) S.bar_phase[slot] ^= 1u;
       S.meta[slot].state = M_EMPTY;
-      produce(P, S, slot ^ 1, buf0 + (size_t)(slot ^ 1) * BUFN);
     }
     const SegDesc sd = P.segs[m.s];
     switch (sd.d) {
