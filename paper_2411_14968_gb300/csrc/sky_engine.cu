@@ -625,6 +625,7 @@ struct Shared {
   u32 pclaim;   // warps past their scan of the current item (the first one produces)
   int pslot;    // buffer slot of the next item
   uint4* pbuf;  // and its buffer
+  u32 abort_seen;  // the launch's abort flag was seen set
 };
 
 // Tile status words of the ordered compaction (decoupled look-back): the
@@ -733,18 +734,24 @@ __device__ void produce(const Params& P, Shared& S, int slot, uint4* buf) {
 // (produce), so the producer's memory round trips delay no warp that still
 // has candidates to test.
 __device__ __forceinline__ void produce_next(const Params& P, Shared& S) {
-  if ((threadIdx.x & 31) == 0 && atomicAdd(&S.pclaim, 1u) == 0) produce(P, S, S.pslot, S.pbuf);
+  if ((threadIdx.x & 31) == 0 && atomicAdd(&S.pclaim, 1u) == 0) {
+    produce(P, S, S.pslot, S.pbuf);
+    // the abort flag for the check after the item, read off its critical path
+    if (ld_vol_u32(P.ctl + C_ABORT)) S.abort_seen = 1;
+  }
   __syncwarp();
 }
 
 template <int D>
 __device__ void load_cand(const SegDesc& sd, u32 pos, bool valid, CandsT<D, R>& c, int r) {
+  // the images are loaded beside the flag, not after it (one round trip)
+  const uint4 h = valid ? __ldg(sd.hc + pos) : make_uint4(0u, 0u, 0u, 0u);
   bool ok = valid && ld_cg_u8(sd.alive + pos);
   c.alive[r] = ok;
   c.was[r] = ok;
   c.pos[r] = pos;
   if (ok) {
-    unpack_dup<D>(__ldg(sd.hc + pos), c.t[r]);
+    unpack_dup<D>(h, c.t[r]);
   } else {
     set_dead<D>(c.t[r]);
   }
@@ -800,20 +807,29 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
   // status words of the earlier tiles (all of which hold smaller tickets, so
   // every one of them is being or has been processed).
   if (!P.cfg.ordered) {
-    // unordered compaction: warp-level slots from one atomic per ballot
+    // unordered compaction: the warp's slots from one atomic
+    bool a[R];
+    u32 m[R];
+    u32 tot = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      u32 pos = gbase + r * 32 + lane;
-      bool a = pos < cs.cend && ld_cg_u8(sd.alive + pos);
-      u32 m = __ballot_sync(FULL, a);
-      u32 base = 0;
-      if (lane == 0 && m) base = atomicAdd(&st->dlen, (u32)__popc(m));
-      base = __shfl_sync(FULL, base, 0);
-      if (a) {
-        u32 slot = base + __popc(m & ((1u << lane) - 1u));
+      const u32 pos = gbase + r * 32 + lane;
+      a[r] = pos < cs.cend && ld_cg_u8(sd.alive + pos);
+      m[r] = __ballot_sync(FULL, a[r]);
+      tot += __popc(m[r]);
+    }
+    u32 base = 0;
+    if (lane == 0 && tot) base = atomicAdd(&st->dlen, tot);
+    base = __shfl_sync(FULL, base, 0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (a[r]) {
+        const u32 pos = gbase + r * 32 + lane;
+        const u32 slot = base + __popc(m[r] & ((1u << lane) - 1u));
         sd.dpos[slot] = pos;
         put_pair_entry<D>(sd.dhc, slot, __ldg(sd.hc + pos));
       }
+      base += __popc(m[r]);
     }
   } else {
   bool a[R];
@@ -965,17 +981,33 @@ __device__ void item_b(const Params& P, const SegDesc& sd, const Meta& mt, const
   }
   __threadfence();
   // the dense tile's flags are final: append its survivors to the window
+  // (the warp's slots from one atomic; the window's order does not matter)
+  u32 wpos[R], wm[R];
+  bool wa[R];
+  u32 tot = 0;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    u32 e = dbase + r * 32 + lane;
-    u32 pos = e < cs.dlen ? __ldcg(sd.dpos + e) : 0;
-    bool a = e < cs.dlen && ld_cg_u8(sd.alive + pos);
-    u32 m = __ballot_sync(FULL, a);
-    u32 base = 0;
-    if (lane == 0 && m) base = atomicAdd(&st->wfill, (u32)__popc(m));
-    base = __shfl_sync(FULL, base, 0);
+    const u32 e = dbase + r * 32 + lane;
+    wpos[r] = e < cs.dlen ? __ldcg(sd.dpos + e) : 0;
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const u32 e = dbase + r * 32 + lane;
+    wa[r] = e < cs.dlen && ld_cg_u8(sd.alive + wpos[r]);
+    wm[r] = __ballot_sync(FULL, wa[r]);
+    tot += __popc(wm[r]);
+  }
+  u32 base = 0;
+  if (lane == 0 && tot) base = atomicAdd(&st->wfill, tot);
+  base = __shfl_sync(FULL, base, 0);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const u32 pos = wpos[r];
+    const bool a = wa[r];
+    const u32 m = wm[r];
+    const u32 slot = base + __popc(m & ((1u << lane) - 1u));
+    base += __popc(m);
     if (a) {
-      u32 slot = base + __popc(m & ((1u << lane) - 1u));
       const float4* src4 = sd.pts + (u64)pos * V;
       float4* dst4 = sd.win + (u64)slot * V;
 #pragma unroll
@@ -1067,6 +1099,7 @@ __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
     S.cursor = 0;
     S.meta[0].state = M_EMPTY;
     S.meta[1].state = M_EMPTY;
+    S.abort_seen = 0;
   }
   __syncthreads();
   if (blockIdx.x == 0 && !prologue(P)) return;
@@ -1124,7 +1157,8 @@ __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
     }
     if (threadIdx.x == 0) atomicAdd(P.ctl + C_PROGRESS, 1u);
     __syncthreads();
-    if (ld_vol_u32(P.ctl + C_ABORT)) {
+    // an abort raised while this item ran is seen after the next one
+    if (S.abort_seen) {
       // the copy of the prefetched item may still be in flight
       const Meta mn = S.meta[slot ^ 1];
       if (mn.state == M_READY && mn.copied) mbar_wait(&S.bar[slot ^ 1], S.bar_phase[slot ^ 1], P.err, P.ctl);
