@@ -220,6 +220,7 @@ __global__ void k_sort_scan(u32* ghist, int npass) {
 // gives every warp its start per digit, and the warp then scatters its keys
 // in the same order, keeping them stable inside each digit.
 constexpr int KPW = RIPT * 32;  // keys per warp of a tile
+constexpr int LBW = 8;          // predecessor status words read per look-back step
 
 __global__ void k_sort_pass(const u64* __restrict__ kin, const u32* __restrict__ vin, u64* __restrict__ kout,
                             u32* __restrict__ vout, u64 n, const u32* __restrict__ n_dev, int shift, u32 mask,
@@ -267,12 +268,31 @@ __global__ void k_sort_pass(const u64* __restrict__ kin, const u32* __restrict__
       *st = ST_INC | tag | c;
     } else {
       *st = ST_AGG | tag | c;
-      u64 i = t - 1;
+      // walk back over the predecessors LBW at a time (their status words
+      // are loaded together, so a walk over k tiles costs k / LBW round
+      // trips), summing aggregates up to the first inclusive prefix
+      u64 i = t;  // tiles below i are still to be read, from i - 1 down
       u64 t0 = 0;
-      for (;;) {
-        const u64 v = *(volatile const u64*)(status + i * RT + tid);
-        const bool ready = ((v >> 32) & 0xffu) == pass_tag && (v >> 62) != 0;
-        if (!ready) {
+      bool fin = false;
+      while (!fin) {
+        u64 v[LBW];
+#pragma unroll
+        for (int w = 0; w < LBW; ++w)
+          v[w] = i > (u64)w ? *(volatile const u64*)(status + (i - 1 - w) * RT + tid) : 0ull;
+        // take the ready words in order, stopping at the first one not ready
+        int adv = 0;
+#pragma unroll
+        for (int w = 0; w < LBW; ++w) {
+          if (fin || adv != w || i <= (u64)w) continue;
+          const bool ready = ((v[w] >> 32) & 0xffu) == pass_tag && (v[w] >> 62) != 0;
+          if (!ready) continue;
+          excl += (u32)v[w];
+          if ((v[w] & ST_INC) || i - 1 - (u64)w == 0) fin = true;
+          adv = w + 1;
+        }
+        if (fin) break;
+        if (adv == 0) {
+          // the nearest predecessor has not counted yet: bounded wait
           if (t0 == 0) {
             t0 = sort_timer();
           } else if (sort_timer() - t0 > WAIT_NS_SORT) {
@@ -282,9 +302,7 @@ __global__ void k_sort_pass(const u64* __restrict__ kin, const u32* __restrict__
           continue;
         }
         t0 = 0;
-        excl += (u32)v;
-        if ((v & ST_INC) || i == 0) break;
-        --i;
+        i -= (u64)adv;
       }
       *st = ST_INC | tag | (excl + c);
     }
