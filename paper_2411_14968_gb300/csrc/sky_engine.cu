@@ -456,14 +456,22 @@ __device__ __forceinline__ u32 ceil_div(u32 a, u32 b) { return (a + b - 1) / b; 
 // ------------------------------------------------------------ work queue
 
 struct Task {
+  u64 tv;       // (first ticket << 32) | 1, written last (release); 0 until published
   u32 s;        // segment
   u32 phase;    // 0: A, 1: B
   u32 tiles;    // candidate tiles of the phase
   u32 items;    // work items (tiles x dominator blocks)
-  u32 ticket0;  // first ticket of the task
-  u32 valid;    // written last
   u32 pad[2];
 };
+
+__device__ __forceinline__ u64 ld_acquire_u64(const u64* p) {
+  u64 v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(u64* p, u64 v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 struct Params {
   const SegDesc* segs;
@@ -534,9 +542,8 @@ __device__ void publish(const Params& P, u32 s, u32 phase, u32 tiles, u32 items)
   t->phase = phase;
   t->tiles = tiles;
   t->items = items;
-  t->ticket0 = t0;
   __threadfence();
-  *(volatile u32*)&t->valid = 1u;
+  st_release_u64(&t->tv, ((u64)t0 << 32) | 1ull);
 }
 
 __device__ void finish_segment(const Params& P) {
@@ -563,11 +570,12 @@ __device__ void start_round(const Params& P, const SegDesc& sd, u32 s, SegState 
   publish(P, s, 0, nx.tiles, nx.tiles * per_tile);
 }
 
-__device__ __forceinline__ u32 task_valid(const Task* t) { return *(const volatile u32*)&t->valid; }
-
 // Finds the task of ticket t: 1 found (*idx), 0 not known yet (retry), -1
 // no more work.  `cursor` is the task of the CTA's previous ticket, a lower
-// bound because a CTA's tickets increase.
+// bound because a CTA's tickets increase.  The task is the last one whose
+// first ticket is <= t: the search gallops forward from the cursor (the
+// CTA's next task is usually near its last one), then bisects; each probe is
+// one acquire load of a task's (first ticket, published) word.
 __device__ int find_task(const Params& P, u32 t, u32* cursor, u32* idx_out) {
   const volatile unsigned long long* q = reinterpret_cast<const volatile unsigned long long*>(P.ctl + C_QUEUE);
   u64 qv = *q;
@@ -579,16 +587,24 @@ __device__ int find_task(const Params& P, u32 t, u32* cursor, u32* idx_out) {
   }
   u32 lo = *cursor, hi = (u32)(qv >> 32);
   if (hi > P.task_cap) hi = P.task_cap;
+  for (u32 step = 1; lo + step < hi; step <<= 1) {
+    const u64 w = ld_acquire_u64(&P.tasks[lo + step].tv);
+    if (!(w & 1ull)) return 0;  // reserved, not yet published
+    if ((u32)(w >> 32) > t) {
+      hi = lo + step;
+      break;
+    }
+    lo += step;
+  }
   while (hi - lo > 1) {
-    const u32 mid = (lo + hi) >> 1;
-    const Task* tm = P.tasks + mid;
-    if (!task_valid(tm)) return 0;
-    __threadfence();
-    if (__ldcg(&tm->ticket0) <= t) lo = mid;
+    const u32 mid = lo + ((hi - lo) >> 1);
+    const u64 w = ld_acquire_u64(&P.tasks[mid].tv);
+    if (!(w & 1ull)) return 0;
+    if ((u32)(w >> 32) <= t) lo = mid;
     else hi = mid;
   }
-  if (!task_valid(P.tasks + lo)) return 0;
-  __threadfence();
+  // orders the reads of the task's fields after its publication
+  if (!(ld_acquire_u64(&P.tasks[lo].tv) & 1ull)) return 0;
   *cursor = lo;
   *idx_out = lo;
   return 1;
@@ -666,7 +682,7 @@ __device__ void produce(const Params& P, Shared& S, int slot, uint4* buf) {
   m.s = __ldcg(&tk->s);
   m.phase = __ldcg(&tk->phase);
   const u32 tiles = __ldcg(&tk->tiles);
-  const u32 l = m.ticket - __ldcg(&tk->ticket0);
+  const u32 l = m.ticket - (u32)(__ldcg(reinterpret_cast<const unsigned long long*>(&tk->tv)) >> 32);
   m.tile = l % tiles;  // block-major: item l = block * tiles + tile
   const u32 b = l / tiles;
   m.tgid = __ldcg(P.tbase + m.s) + m.tile;
