@@ -706,15 +706,9 @@ __device__ void produce(const Params& P, Shared& S, int slot, uint4* buf) {
     } else {
       // the dense list is in position (= score) order: a candidate of dense
       // tile t can only be dominated by dense entries up to the end of the
-      // tile, extended over a run of scores equal to its last one
-      const u32 tend = P.cfg.ordered ? min(dlen, (m.tile + 1) * TILE) : dlen;
-      u32 e = tend;
-      if (tend < dlen) {
-        const float* sc = sd->score;
-        const float last = __ldg(sc + __ldcg(sd->dpos + tend - 1));
-        const float next = __ldg(sc + __ldcg(sd->dpos + tend));
-        if (next == last) e = dlen;  // a tie straddles the tile end (rare): all of the list
-      }
+      // tile, extended over a run of scores equal to its last one (the end
+      // the last phase-A tile wrote into the tile's status word)
+      const u32 e = P.cfg.ordered ? ld_cg_u32(P.tstat + m.tgid) : dlen;
       m.base = (b - wbB) * DB;
       m.cnt = m.base < e ? min(DB, e - m.base) : 0;
       m.dense = 1;
@@ -918,17 +912,38 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
   fence_proxy_async();
   __syncthreads();
   if (threadIdx.x == 0) {
-    u32 old = atomicAdd(&st->done_a, 1u);
-    if (old == cs.tiles - 1) {
-      // last tile of phase A: every tile has finished its look-back, so the
-      // status words are cleared for the next round; then publish phase B,
-      // or the next round if nothing survived
+    const u32 old = atomicAdd(&st->done_a, 1u);
+    S.flag = old == cs.tiles - 1;
+    if (S.flag) {
       __threadfence();
-      if (P.cfg.ordered) {
-        u32* stat = P.tstat + __ldcg(P.tbase + s);
-        for (u32 j = 0; j < cs.tiles; ++j) stat[j] = 0;
+      S.tile_base = atomicAdd(&st->dlen, 0u);
+    }
+  }
+  __syncthreads();
+  if (!S.flag) return;
+  const u32 dl = S.tile_base;
+  if (P.cfg.ordered) {
+    // last tile of phase A: every tile has finished its look-back, so its
+    // status word is free.  It now holds the dense tile's end for phase B:
+    // the tile's last position, or the whole list when a run of equal
+    // scores straddles it (zero past the dense tiles, for the next round)
+    u32* stat = P.tstat + __ldcg(P.tbase + s);
+    for (u32 j = threadIdx.x; j < cs.tiles; j += THREADS) {
+      const u32 tend = min(dl, (j + 1) * TILE);
+      u32 e = j * TILE < dl ? tend : 0u;
+      if (e && tend < dl) {
+        const float last = __ldg(sd.score + __ldcg(sd.dpos + tend - 1));
+        const float next = __ldg(sd.score + __ldcg(sd.dpos + tend));
+        if (next == last) e = dl;
       }
-      const u32 dl = atomicAdd(&st->dlen, 0u);
+      stat[j] = e;
+    }
+    __threadfence();
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    {
+      // publish phase B, or the next round if nothing survived
       if (dl == 0) {
         SegState nx;
         nx.cur = cs.cend;
@@ -1037,7 +1052,12 @@ __device__ void item_b(const Params& P, const SegDesc& sd, const Meta& mt, const
   if (threadIdx.x == 0) {
     u32 old = atomicAdd(&st->done_b, 1u);
     if (old == dtiles - 1) {
-      // last dense tile: the next round
+      // last dense tile: clear the tile ends for the next round's phase A,
+      // then the next round
+      if (P.cfg.ordered) {
+        u32* stat = P.tstat + __ldcg(P.tbase + s);
+        for (u32 j = 0; j < dtiles; ++j) stat[j] = 0;
+      }
       __threadfence();
       SegState nx;
       nx.cur = cs.cend;
