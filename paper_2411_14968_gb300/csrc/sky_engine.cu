@@ -40,12 +40,12 @@
 // reserves a contiguous range of tickets with one 64-bit atomic (task index
 // and ticket range together, so both orders agree) and then marks the task
 // valid.  A CTA claims tickets one at a time and finds the task of its
-// ticket by binary search over the published tasks.  The CTA that completes
-// the last tile of a phase publishes the segment's next phase (or its next
-// round's phase A, or finishes the segment); when the last segment finishes,
-// the CTAs still waiting for tickets leave.  Segments of different sizes and
-// queries of a batch thus overlap freely, and a segment's long phase never
-// holds up the others.
+// ticket by a galloping search from the task of its previous ticket.  The
+// CTA that completes the last tile of a phase publishes the segment's next
+// phase (or its next round's phase A, or finishes the segment); when the
+// last segment finishes, the CTAs still waiting for tickets leave.
+// Segments of different sizes and queries of a batch thus overlap freely,
+// and a segment's long phase never holds up the others.
 //
 // Dominance test.  Every point carries, next to its FP32 attributes, their
 // round-down FP16 images packed two per 32-bit word.  Round-down is monotone,
