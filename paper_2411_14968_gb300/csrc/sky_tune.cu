@@ -152,11 +152,10 @@ sky_status tune(sky_ctx* ctx, const sky_query* queries, uint32_t nq, uint32_t ma
     }
     if (!changed) break;
   }
-  // The search compares the faster of two runs per candidate, and a batch's
-  // time varies from run to run (the work queue's order changes which
-  // dominators meet which candidates first), so a lucky run can pick a worse
-  // candidate.  Confirm the winner against the starting knobs with the
-  // median of CONFIRM interleaved runs each.
+  // A batch's time varies from run to run (the work queue's order changes
+  // which dominators meet which candidates first), so even a median of
+  // three can favour a worse candidate.  Confirm the winner against the
+  // starting knobs with the median of CONFIRM interleaved runs each.
   const bool moved = cur.chunk_min != start.chunk_min || cur.chunk_max != start.chunk_max ||
                      cur.chunk_alpha_x4 != start.chunk_alpha_x4 || cur.dom_block != start.dom_block;
   if (status == SKY_OK && moved) {
