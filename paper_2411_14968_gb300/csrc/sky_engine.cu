@@ -335,8 +335,8 @@ __device__ __forceinline__ u32 scan_steps(const uint4* sb, u32 j, u32 cnt, const
                                           CandsT<D, RR>& c, u32* n_alive) {
   constexpr int V = vec_of(D);
   // dominator pairs per step: more with fewer candidate slots (the step's
-  // fixed cost is spread over more tests); at d = 8 the kernel needs 122
-  // registers, within the budget of four 128-thread CTAs per SM
+  // fixed cost is spread over more tests); the kernel needs 120 registers,
+  // within the budget of four 128-thread CTAs per SM
   constexpr int UP = 2 * (RR == 1 ? 2 : 1);
   // the last step may read pairs past the block's end (whatever the
   // buffer held): the FP32 path checks the bound, so a spurious pass there
