@@ -185,13 +185,19 @@ __global__ void k_sort_hist(const u64* __restrict__ k, u64 n, const u32* __restr
   __syncthreads();
   n = radix_count(n, n_dev);
   const u64 base = (u64)blockIdx.x * RTILE;
+  // the tile's keys are loaded together (one memory latency), then counted
+  u64 kr[RIPT];
+#pragma unroll
   for (int r = 0; r < RIPT; ++r) {
     const u64 e = base + (u64)r * RT + tid;
-    if (e >= n) break;
-    const u64 key = k[e];
+    kr[r] = e < n ? k[e] : 0ull;
+  }
+#pragma unroll
+  for (int r = 0; r < RIPT; ++r) {
+    if (base + (u64)r * RT + tid >= n) break;
     for (int p = 0; p < npass; ++p) {
       const u32 mask = p == npass - 1 ? (1u << last_bits) - 1u : 0xffu;
-      atomicAdd(&h[p][(u32)(key >> (lo_bit + 8 * p)) & mask], 1u);
+      atomicAdd(&h[p][(u32)(kr[r] >> (lo_bit + 8 * p)) & mask], 1u);
     }
   }
   __syncthreads();
@@ -239,12 +245,27 @@ __global__ void k_sort_pass(const u64* __restrict__ kin, const u32* __restrict__
   const u64 base = t * RTILE;
   if (base >= n) return;
   const u64 wbase = base + (u64)warp * KPW;
+  // the warp's keys and values are loaded together up front (one memory
+  // latency for the tile instead of one per iteration of the passes below)
+  u64 kr[RIPT];
+  u32 vr[RIPT];
+#pragma unroll
+  for (int r = 0; r < RIPT; ++r) {
+    const u64 e = wbase + (u64)r * 32 + lane;
+    kr[r] = e < n ? kin[e] : 0ull;
+  }
+#pragma unroll
+  for (int r = 0; r < RIPT; ++r) {
+    const u64 e = wbase + (u64)r * 32 + lane;
+    vr[r] = e < n ? vin[e] : 0u;
+  }
   // this warp's digit counts (a digit's leader lane adds its peers; leaders
   // of one iteration hold distinct digits, so no atomics are needed)
+#pragma unroll
   for (int r = 0; r < RIPT; ++r) {
     const u64 e = wbase + (u64)r * 32 + lane;
     const bool valid = e < n;
-    const u32 dg = valid ? (u32)(kin[e] >> shift) & mask : 0xffffffffu;
+    const u32 dg = valid ? (u32)(kr[r] >> shift) & mask : 0xffffffffu;
     const u32 peers = __match_any_sync(FULL, dg);
     if (valid && lane == __ffs(peers) - 1) s_w[warp][dg] += __popc(peers);
     __syncwarp();
@@ -310,11 +331,12 @@ __global__ void k_sort_pass(const u64* __restrict__ kin, const u32* __restrict__
   }
   __syncthreads();
   // stable scatter, in the order of the count pass
+#pragma unroll
   for (int r = 0; r < RIPT; ++r) {
     const u64 e = wbase + (u64)r * 32 + lane;
     const bool valid = e < n;
-    const u64 key = valid ? kin[e] : 0;
-    const u32 val = valid ? vin[e] : 0;
+    const u64 key = kr[r];
+    const u32 val = vr[r];
     const u32 dg = valid ? (u32)(key >> shift) & mask : 0xffffffffu;
     const u32 peers = __match_any_sync(FULL, dg);
     u32 pos = 0;
