@@ -1,9 +1,9 @@
 """Timing of N independent replicas, one process per GPU.
 
 The partitioned skyline shards naturally (partitions are independent until
-the final phase), but every run of this build gets one GPU, so several GPUs
-run independent replicas of the same workload (weak scaling): no data moves
-between ranks.  What the ranks share is only the measurement protocol -- a
+the final phase), but no cross-GPU exchange step is implemented: several
+GPUs run independent replicas of the same workload (weak scaling), and no
+data moves between ranks.  What the ranks share is only the measurement protocol -- a
 barrier on both sides of the timed region and the maximum of the per-rank
 times -- which this module provides over torch.distributed (NCCL on GPUs,
 gloo on CPU for the tests).
