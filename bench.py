@@ -136,6 +136,25 @@ def load_workcounts():
         return json.load(fh)["variants"]
 
 
+def host_cpu() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name, or the Arm
+    implementer and part codes), with the core count."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            info = fh.read()
+        for key in ("model name", "Model", "CPU part"):
+            for ln in info.splitlines():
+                if ln.split(":")[0].strip() == key:
+                    model = f"{key}: {ln.split(':', 1)[1].strip()}"
+                    break
+            if model:
+                break
+    except OSError:
+        pass
+    return f"{model or 'unknown'}; {os.cpu_count()} logical cores"
+
+
 def cpu_oracle_sample(n_sample: int, threads: int = 1):
     """Times the CPU oracle (C, as it stands) on the same variants over the
     first n_sample points of the same generator.  threads > 1 spreads
@@ -180,7 +199,8 @@ def reference_arm(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": {"workload": WORKLOAD, "sample_points": n_sample},
         "cpu_baseline": {"value": value, "unit": "points/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {n_sample} points of the same generator, 4 variants per step"},
+                         "sample": f"first {n_sample} points of the same generator, 4 variants per step",
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -463,7 +483,8 @@ def gpu_arm(args, rank, world, local):
         n_sample = 100_000
         secs, pts = cpu_oracle_sample(n_sample)
         cpu = {"value": pts / secs, "unit": "points/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {n_sample} points of the same generator, the 4 variants once ({secs:.1f} s)"}
+               "sample": f"first {n_sample} points of the same generator, the 4 variants once ({secs:.1f} s)",
+               "host": host_cpu()}
         from oracle import oracle as O
         threads = min(O.max_threads(), os.cpu_count() or 1)
         if threads > 1:
