@@ -108,7 +108,8 @@ typedef struct {
   uint64_t local_union;        /* |u| = sum of local skyline sizes */
   uint64_t skyline;            /* |Sky(r)| */
   double ms_total;             /* device time of the whole call (0 unless timing is on) */
-  double ms_phase[6];          /* prep+sort, filters, local, merge, output, host copies */
+  double ms_phase[6];          /* prep+sort (after a host input's copy to the device), filters, local,
+                                  merge, output, host copies */
   uint64_t launches;           /* CUDA kernels the call launched */
   double ms_dom_local;         /* device time of the local-skyline dominance launches (timing on) */
   double ms_dom_merge;         /* device time of the final-phase dominance launch (timing on) */

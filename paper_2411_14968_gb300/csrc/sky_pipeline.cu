@@ -593,6 +593,12 @@ sky_status Runner::enqueue(BatchState& B) {
   };
   auto qstream = [&](const Work& w) -> cudaStream_t { return multi ? aux_[(&w - ws.data()) % NAUX] : stream; };
   record(0, B);
+  // a host input's copy to the device runs on its query's stream at the
+  // start of the partition phase, so that later queries' copies overlap
+  // earlier queries' partitioning
+  record(1, B);
+
+  // ---- Partition(r, p): keys, sort, gather (Algorithm 2 first phase)
   CK(fork());
   for (auto& w : ws) {
     if (w.q->n == 0) continue;
@@ -602,15 +608,6 @@ sky_status Runner::enqueue(BatchState& B) {
       CK(cudaMemcpyAsync(w.b.X, w.q->points, w.q->n * w.q->d * sizeof(float), cudaMemcpyHostToDevice, st));
       w.X = w.b.X;
     }
-  }
-  CK(join());
-  record(1, B);
-
-  // ---- Partition(r, p): keys, sort, gather (Algorithm 2 first phase)
-  CK(fork());
-  for (auto& w : ws) {
-    if (w.q->n == 0) continue;
-    const cudaStream_t st = qstream(w);
     const Plan& pl = w.pl;
     Bufs& b = w.b;
     const u64 n = pl.n;
