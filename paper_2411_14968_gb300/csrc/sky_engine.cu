@@ -653,10 +653,12 @@ constexpr u32 TS_AGG = 1u << 30, TS_INC = 2u << 30, TS_VAL = TS_AGG - 1;
 // retire in one call before it hands the CTA a ticket still pending.
 constexpr int SKIP_MAX = 32;
 
-// Producer (thread 0 only, never blocks): claims a ticket for buffer `slot`
-// if it has none, and once the ticket's task is known plans the item and
-// starts the bulk copy of its dominator block's FP16 images.  The buffer is
-// free: every warp has finished the item that used it.  A phase-B item whose
+// Producer (one thread at a time: thread 0 while the CTA waits for work, else
+// lane 0 of the warp that finished the current item first; never blocks):
+// claims a ticket for buffer `slot` if it has none, and once the ticket's
+// task is known plans the item and starts the bulk copy of its dominator
+// block's FP16 images.  The buffer is free: every warp has finished the item
+// that used it.  A phase-B item whose
 // dense block lies past its tile's triangular bound tests nothing: the
 // producer counts it towards its tile's completion itself and claims the
 // next ticket, unless the item is the one that completes the tile (then the
