@@ -281,6 +281,64 @@ def test_random_partitions_equinumerous(oracle_mod):
     assert len(np.unique(a[: n // p])) == p
 
 
+GAMMA = 0x9E3779B97F4A7C15  # SplitMix64's state increment (Steele, Lea & Flood 2014)
+
+
+def test_random_hand_instances(oracle_mod):
+    # Section 3.1 as read here: pid = floor(rank * p / N), rank of the point's
+    # SplitMix64 key in ascending order (ties by index).  The keys below are
+    # the published outputs pinned in test_splitmix64_published_outputs:
+    #   seed 0: key(0) = 0xE220..., key(1) = 0x6E78..., key(2) = 0x06C4...
+    # so the ascending order is point 2, 1, 0 and the ranks are (2, 1, 0).
+    #   p = 3: floor(r * 3 / 3) = r           -> (2, 1, 0)
+    #   p = 2: floor(r * 2 / 3): r 0,1 -> 0, r 2 -> 1 -> (1, 0, 0)
+    # (rank % p would give (0, 1, 0); a descending rank or index order (0, 0, 1).)
+    assert oracle_mod.assign_random(3, 3, 0).tolist() == [2, 1, 0]
+    assert oracle_mod.assign_random(3, 2, 0).tolist() == [1, 0, 0]
+    assert oracle_mod.assign_random(3, 1, 0).tolist() == [0, 0, 0]
+    # Starting the state one increment earlier (seed = -GAMMA mod 2^64) shifts
+    # the stream by one: key(i) = published output i - 1 for i >= 1, and key(0)
+    # mixes the state 0, which every xor-shift and multiply keeps at 0.  Keys
+    # (0, 0xE220..., 0x6E78..., 0x06C4...): ascending order 0, 3, 2, 1, so the
+    # ranks of points 0..3 are (0, 3, 2, 1).
+    #   p = 2: floor(r / 2)      -> (0, 1, 1, 0)
+    #   p = 3: floor(3 r / 4): r 0 -> 0, 1 -> 0, 2 -> 1, 3 -> 2 -> (0, 2, 1, 0)
+    #   p = 4: r                 -> (0, 3, 2, 1)
+    s = (-GAMMA) % (1 << 64)
+    assert oracle_mod.splitmix64(s, 0) == 0
+    assert oracle_mod.splitmix64(s, 1) == 0xE220A8397B1DCDAF
+    assert oracle_mod.assign_random(4, 2, s).tolist() == [0, 1, 1, 0]
+    assert oracle_mod.assign_random(4, 3, s).tolist() == [0, 2, 1, 0]
+    assert oracle_mod.assign_random(4, 4, s).tolist() == [0, 3, 2, 1]
+
+
+def test_sliced_hand_instance_run_across_a_boundary(oracle_mod):
+    # Section 3.4 as read here: order by (x_0, f, index), nominal pid =
+    # floor(rank * p / N), and a run of equal (x_0, f) takes the pid of its
+    # first member (the boundary moves to the end of the run).
+    x = np.array([[0.25, 0.75],   # 0: f = 1.0
+                  [0.75, 0.0],    # 1: f = 0.75
+                  [0.0, 1.0],     # 2: f = 1.0
+                  [0.25, 0.5],    # 3: f = 0.75
+                  [0.5, 0.5],     # 4: f = 1.0
+                  [0.25, 0.5]],   # 5: f = 0.75 (a copy of 3)
+                 np.float32)
+    # Order: 2 (x0 0), then x0 = 0.25 by f: 3, 5 (f 0.75, by index), 0 (f 1.0),
+    # then 4 (x0 0.5), 1 (x0 0.75): ranks of points 0..5 = (3, 5, 0, 1, 4, 2).
+    # Points 3 and 5 (ranks 1, 2) are one run, which starts at rank 1, so the
+    # run-start ranks are (3, 5, 0, 1, 4, 1).
+    #   p = 3: floor(s / 2) -> (1, 2, 0, 0, 2, 0)   (rank 2 alone would be slice 1)
+    #   p = 2: floor(s / 3) -> (1, 1, 0, 0, 1, 0)
+    #   p = 6: s            -> (3, 5, 0, 1, 4, 1)   (slice 2 stays empty)
+    assert oracle_mod.assign_sliced(x, 3).tolist() == [1, 2, 0, 0, 2, 0]
+    assert oracle_mod.assign_sliced(x, 2).tolist() == [1, 1, 0, 0, 1, 0]
+    assert oracle_mod.assign_sliced(x, 6).tolist() == [3, 5, 0, 1, 4, 1]
+    # slicing on attribute 1: order 1 (x1 0), 3, 5, 4 (x1 0.5; f 0.75, 0.75,
+    # 1.0), 0 (0.75), 2 (1.0); run 3, 5 starts at rank 1; ranks (4, 0, 5, 1, 3, 2)
+    # -> run starts (4, 0, 5, 1, 3, 1); p = 3: floor(s / 2) -> (2, 0, 2, 0, 1, 0)
+    assert oracle_mod.assign_sliced(x, 3, dim=1).tolist() == [2, 0, 2, 0, 1, 0]
+
+
 def test_sliced_sizes_and_dominance_order(oracle_mod):
     x = datagen.anticorrelated(4000, 4, 3)
     pid = oracle_mod.assign_sliced(x, 8)
