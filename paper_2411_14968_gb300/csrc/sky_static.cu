@@ -16,10 +16,13 @@
 // In host code the array's name only stands in for it: its device address
 // is taken with cudaGetSymbolAddress once per device, on the first call made
 // with that device current, and cached.  That first call should therefore
-// come before any stream capture.  Every call shares the array and finds the
-// previous call's contents in it, so the call clears what must start at zero
-// itself; calls whose work overlaps on the GPU (several host threads, or
-// several streams) race on the array and must not be made.
+// come before any stream capture.  Inputs and outputs must be device memory
+// of the current device (or managed memory); memory of another GPU is
+// refused, since the kernels would read or write it through the peer path.
+// Every call shares the array and finds the previous call's contents in it,
+// so the call clears what must start at zero itself; calls whose work
+// overlaps on the GPU (several host threads, or several streams) race on
+// the array and must not be made.
 #include <cstring>
 #include <mutex>
 #include "../../include/skyline.h"
@@ -69,14 +72,31 @@ __global__ void k_static_pack(const float* __restrict__ X, u32 n, float4* __rest
   alive[i] = 1;
 }
 
-// Device address of the array on the current device (set-up on first use).
+// Device address of the array on the current device.  Set-up, on the first
+// call with a device current: cudaGetSymbolAddress, cached per device.  A
+// cached address is used only while the runtime still reports it as device
+// memory of the current device; after a cudaDeviceReset the module (and the
+// array) is loaded again, the old address is no longer valid, and the set-up
+// runs again.
+bool is_current_device_mem(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  int cur = -1;
+  if (a.type != cudaMemoryTypeDevice || cudaGetDevice(&cur) != cudaSuccess) return false;
+  return a.device == cur;
+}
+
 cudaError_t scratch_address(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> g(g_mu);
-  if (!g_addr[dev]) {
+  if (!g_addr[dev] || !is_current_device_mem(g_addr[dev])) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return e;
@@ -84,15 +104,6 @@ cudaError_t scratch_address(unsigned char** out) {
   }
   *out = g_addr[dev];
   return cudaSuccess;
-}
-
-bool on_device(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -107,7 +118,7 @@ extern "C" sky_status sky_skyline_static(const float* points, uint64_t n, uint32
   if (d < 1 || d > 8) return SKY_EINVAL;
   if (n > SKY_STATIC_MAX_POINTS) return SKY_EINVAL;
   if (n == 0) return SKY_OK;
-  if (!points || !out_idx || !on_device(points) || !on_device(out_idx)) return SKY_EINVAL;
+  if (!points || !out_idx || !is_current_device_mem(points) || !is_current_device_mem(out_idx)) return SKY_EINVAL;
   if (scan_tmp_words(n) > TMP_WORDS) return SKY_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   unsigned char* base = nullptr;
