@@ -27,6 +27,22 @@ extern "C" {
 sky_status sky_probe_compare_rate(sky_ctx* ctx, uint32_t iterations, double* compares_per_s,
                                   uint32_t* sm_count);
 
+/* Test hook of the engine's bounded waits (the paper has no counterpart; it
+   exists so that a test can show that a device-side wait which never ends
+   is turned into an error status without faulting or hanging the GPU).
+   Arms the context's next sky_skyline / sky_skyline_ex / sky_skyline_batch
+   call only (the call after it runs normally again): every wait of the
+   persistent engine -- for a bulk copy, for a ticket's task, for a
+   preceding tile's count -- gives up after wait_limit_ns nanoseconds
+   without progress anywhere in the launch (instead of 4 s), and, when
+   withhold_task >= 1, the withhold_task-th task that an engine launch of
+   that call publishes keeps its tickets but is never marked published, so
+   the CTAs that draw those tickets wait until the limit runs out.  The
+   armed call then returns SKY_ETIMEOUT (or SKY_OK when the launch has
+   fewer tasks); the context stays usable.  Errors: SKY_EINVAL (NULL
+   context, wait_limit_ns below 1 ms). */
+sky_status sky_diag_engine_wait_test(sky_ctx* ctx, uint64_t wait_limit_ns, uint32_t withhold_task);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,7 +64,8 @@
 // staged block with broadcast
 // shared loads and leaves the item when a ballot shows all its candidates
 // dead.  Every wait (mbarrier, waiting for a ticket's task) is bounded: it
-// gives up with ERR_TIMEOUT when no item anywhere has completed for WAIT_NS.
+// gives up with ERR_TIMEOUT when no item anywhere has completed for WAIT_NS
+// (a launch may set a shorter limit: EngineCfg::wait_ns).
 #include <algorithm>
 #include "sky_internal.cuh"
 
@@ -87,7 +88,7 @@ constexpr u32 DBMAX = 2048;             // dominator block capacity (points)
 // and only with one phase-A item per tile is that item's ticket above every
 // item of the tiles before it, so the CTAs it waits for never wait for it.
 constexpr u32 A_BLOCKS = 1;
-constexpr u64 WAIT_NS = 4000000000ull;  // bound of every wait (without progress)
+constexpr u64 WAIT_NS = 4000000000ull;  // default bound of every wait (without progress)
 
 // Control words of a launch (zeroed by the host before it).  The queue word
 // is 64-bit: (tasks published << 32) | tickets reserved.
@@ -133,11 +134,11 @@ __device__ __forceinline__ bool mbar_try_wait(u64* bar, u32 parity) {
 }
 // Bounded wait for phase `parity` of the barrier.  On timeout the error and
 // abort words are set and false is returned.
-__device__ bool mbar_wait(u64* bar, u32 parity, u32* err, u32* ctl) {
+__device__ bool mbar_wait(u64* bar, u32 parity, u64 limit_ns, u32* err, u32* ctl) {
   if (mbar_try_wait(bar, parity)) return true;
   u64 t0 = globaltimer();
   while (!mbar_try_wait(bar, parity)) {
-    if (globaltimer() - t0 > WAIT_NS) {
+    if (globaltimer() - t0 > limit_ns) {
       atomicOr(err, ERR_TIMEOUT);
       atomicExch(ctl + C_ABORT, 1u);
       return false;
@@ -147,6 +148,12 @@ __device__ bool mbar_wait(u64* bar, u32 parity, u32* err, u32* ctl) {
 }
 // Generic-proxy writes of global memory made visible to later bulk copies.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+// A thread's generic-proxy reads of a staging buffer ordered before the
+// async-proxy writes of a later bulk copy into the same buffer (issued by
+// one thread after a CTA barrier that every reader has passed).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 
 
 // ------------------------------------------------------------ dominance test
@@ -487,6 +494,7 @@ struct Params {
   u32 task_cap;
   u32* ctl;
   u32* err;
+  u64 wait_ns;     // bound of every wait without progress
 };
 
 __device__ __forceinline__ void abort_launch(const Params& P, u32 code) {
@@ -537,6 +545,10 @@ __device__ void publish(const Params& P, u32 s, u32 phase, u32 tiles, u32 items)
     abort_launch(P, ERR_CAPACITY);
     return;
   }
+  // test hook (EngineCfg::withhold_task): the task keeps its tickets but is
+  // never marked published, so the CTAs that draw them wait until the
+  // bounded wait gives up
+  if (P.cfg.withhold_task && idx + 1 == P.cfg.withhold_task) return;
   Task* t = P.tasks + idx;
   t->s = s;
   t->phase = phase;
@@ -798,6 +810,9 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
       scan_smem<D>(staged, cnt, src, sd.pts, c, S.scode[warp], S.spos[warp], sd.alive);
     }
   }
+  // the staged buffer is refilled by a bulk copy once every warp is past
+  // the barrier below
+  fence_proxy_async_smem();
   produce_next(P, S);
   __syncthreads();
   // with one item per tile (always so while A_BLOCKS is 1) the item
@@ -883,7 +898,7 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
         if (t0 == 0 || now != seen) {
           seen = now;
           t0 = globaltimer();
-        } else if (globaltimer() - t0 > WAIT_NS || ld_vol_u32(P.ctl + C_ABORT)) {
+        } else if (globaltimer() - t0 > P.wait_ns || ld_vol_u32(P.ctl + C_ABORT)) {
           abort_launch(P, ERR_TIMEOUT);
           break;
         }
@@ -996,6 +1011,7 @@ __device__ void item_b(const Params& P, const SegDesc& sd, const Meta& mt, const
       scan_smem<D>(staged, cnt, src, sd.pts, c, S.scode[warp], S.spos[warp], sd.alive);
     }
   }
+  fence_proxy_async_smem();  // as in item_a
   produce_next(P, S);
   __syncthreads();
   if (per_tile > 1) {
@@ -1165,7 +1181,7 @@ __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
         if (t0 == 0 || now != seen) {
           seen = now;
           t0 = globaltimer();
-        } else if (globaltimer() - t0 > WAIT_NS) {
+        } else if (globaltimer() - t0 > P.wait_ns) {
           abort_launch(P, ERR_TIMEOUT);
           S.meta[slot].state = M_DONE;
           break;
@@ -1176,7 +1192,7 @@ __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
     __syncthreads();
     const Meta m = S.meta[slot];
     if (m.state != M_READY) break;
-    if (m.copied && !mbar_wait(&S.bar[slot], S.bar_phase[slot], P.err, P.ctl)) break;
+    if (m.copied && !mbar_wait(&S.bar[slot], S.bar_phase[slot], P.wait_ns, P.err, P.ctl)) break;
     __syncthreads();
     if (threadIdx.x == 0) {
       if (m.copied) S.bar_phase[slot] ^= 1u;
@@ -1199,7 +1215,8 @@ __global__ void __launch_bounds__(THREADS) k_engine(Params P) {
     if (S.abort_seen) {
       // the copy of the prefetched item may still be in flight
       const Meta mn = S.meta[slot ^ 1];
-      if (mn.state == M_READY && mn.copied) mbar_wait(&S.bar[slot ^ 1], S.bar_phase[slot ^ 1], P.err, P.ctl);
+      if (mn.state == M_READY && mn.copied)
+        mbar_wait(&S.bar[slot ^ 1], S.bar_phase[slot ^ 1], P.wait_ns, P.err, P.ctl);
       break;
     }
   }
@@ -1236,6 +1253,7 @@ cudaError_t engine_run(const SegDesc* segs_dev, u32 nseg, const EngineCfg& cfg, 
   P.task_cap = (u32)w.task_cap;
   P.ctl = w.ctl;
   P.err = err;
+  P.wait_ns = cfg.wait_ns ? cfg.wait_ns : WAIT_NS;
   size_t smem = 2 * ((size_t)cfg.dom_block + STAGE_PAD) * sizeof(uint4);
   cudaError_t e = cudaFuncSetAttribute(k_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -229,6 +229,12 @@ struct EngineCfg {
   // tiles) so phase B tests only the lower-score half of the dense square;
   // pays off for large chunks (the merge), costs waits for many small ones
   u32 ordered;
+  // Test hooks, zero unless set through sky_diag_engine_wait_test: the bound
+  // of every device-side wait without progress (0 = the built-in 4 s), and
+  // the 1-based index of a task of the launch that is reserved but never
+  // published (0 = none), which makes the waits for it run out.
+  u64 wait_ns;
+  u32 withhold_task;
 };
 
 struct EngineWork {
@@ -269,8 +275,10 @@ struct SegArrays {
   u32* dpos;
   uint4* dhc;
 };
+// nonempty (may be NULL): incremented once per partition that holds a point
+// (before Grid Filtering).
 cudaError_t launch_build_segs(const u32* seg_off, u32 P, const u8* dropped, const SegArrays& a, int d,
-                              SegDesc* segs, cudaStream_t st);
+                              SegDesc* segs, u32* nonempty, cudaStream_t st);
 cudaError_t launch_build_one_seg(const SegArrays& a, const u32* n_dev, int d, SegDesc* seg, cudaStream_t st);
 cudaError_t launch_fold_max(const u32* src, u32* dst, cudaStream_t st);
 
