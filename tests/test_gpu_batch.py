@@ -107,14 +107,17 @@ def test_autotune_batch_keeps_results(ctx):
         np.testing.assert_array_equal(g, w)
 
 
-def test_graph_replay_matches_and_reads_inputs_at_replay(ctx):
+def test_graph_replay_matches_and_reads_inputs_at_replay(ctx, oracle_mod):
     import torch
     from paper_2411_14968_gb300 import native
+    O = oracle_mod
     x0 = [datagen.anticorrelated(40000, 6, 71), datagen.independent(20000, 4, 72)]
     x1 = [datagen.anticorrelated(40000, 6, 73), datagen.independent(20000, 4, 74)]
     ps = [native.make_params(scheme="sliced", p=8, rep="sorted"), native.make_params(scheme="grid", slices=[3] * 4)]
-    want0 = [ctx.skyline(x, params=p) for x, p in zip(x0, ps)]
-    want1 = [ctx.skyline(x, params=p) for x, p in zip(x1, ps)]
+    ops = [dict(scheme=O.SLICED, p=8, rep=O.REP_SORTED), dict(scheme=O.GRID, slices=[3] * 4)]
+    # the expected sets are the oracle's (Algorithm 2 with the same options)
+    want0 = [O.partitioned(x, **kw)["indices"] for x, kw in zip(x0, ops)]
+    want1 = [O.partitioned(x, **kw)["indices"] for x, kw in zip(x1, ops)]
     xt = [torch.from_numpy(x).cuda() for x in x0]
     g = ctx.capture(list(zip(xt, ps)))
     for _ in range(2):
