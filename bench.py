@@ -46,7 +46,6 @@ VARIANTS = [
 WORKLOAD = (f"anticorrelated FP32 N={N} d={D} seed={SEED}; Sliced p=64 and Angular (4,2,2,2,2), "
             "each without and with 1 Sorted representative per partition; sequential merge")
 L2_FLUSH_BYTES = 256 << 20
-SM_COUNT = 152
 
 
 from paper_2411_14968_gb300.replicas import dist_env  # noqa: E402
@@ -206,15 +205,20 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-SERVE_QUERIES = 300
+SERVE_QUERIES = 2000
 SERVE_SEED = 5
+SERVE_LOADS = (0.5, 0.8, 1.25)  # offered load, x the plain path's measured capacity
 
 
 def serving_pool(dev_pin: bool):
     """Seeded datasets the serving queries are drawn from: per (kind, d) one
     pool of 2^20 i.i.d. points; a query of N points is a window of N
-    consecutive rows at a seeded offset (rows are i.i.d., so a window is a
-    sample of the same distribution)."""
+    consecutive rows at a seeded offset.  The generators draw every row
+    independently, so a window of N rows has exactly the distribution of a
+    freshly generated N-point dataset of that kind and d; what windows do not
+    give is independence between two queries whose windows overlap, which
+    no per-query quantity measured here depends on.  Generating the 2,000
+    queries' ~3e8 points one dataset at a time would take minutes."""
     import torch
     from paper_2411_14968_gb300 import datagen
     pool = {}
@@ -264,12 +268,13 @@ def run_serving(ctx, native, queries, arrivals, exec_, workers, max_batch):
     return np.array(lat), span, float(np.mean(batch))
 
 
-def serving_leg(native, local):
+def serving_leg(native, local, num_queries=SERVE_QUERIES):
     """Continuous batching vs one query at a time with one launch per
-    partition, on the same Poisson arrival trace."""
+    partition, on the same Poisson arrival traces, at offered loads of 0.5,
+    0.8 and 1.25 x the plain path's measured capacity."""
     from paper_2411_14968_gb300 import datagen
     pool = serving_pool(True)
-    queries = serving_queries(SERVE_QUERIES, pool, native)
+    queries = serving_queries(num_queries, pool, native)
     total_pts = sum(x.shape[0] for x, _ in queries)
     ctx = native.Context(local)
     try:
@@ -279,27 +284,42 @@ def serving_leg(native, local):
         # capacity of the plain one-at-a-time path (back-to-back)
         _, span_cap, _ = run_serving(ctx, native, queries, None, "plain", 1, 1)
         cap_qps = len(queries) / span_cap
-        rate = 0.8 * cap_qps
-        arr = datagen.poisson_arrivals(len(queries), rate, SERVE_SEED)
-        res = {}
-        for name, exec_, w, mb in (("plain", "plain", 1, 1), ("batched", "persistent", 2, 64)):
-            lat, span, mean_batch = run_serving(ctx, native, queries, arr, exec_, w, mb)
-            res[name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                         "mean_ms": float(lat.mean()), "points_per_s": total_pts / span,
-                         "queries_per_s": len(queries) / span, "mean_batch_queries": mean_batch}
+        loads = []
+        for load in SERVE_LOADS:
+            rate = load * cap_qps
+            arr = datagen.poisson_arrivals(len(queries), rate, SERVE_SEED)
+            row = {"load": load, "offered_queries_per_s": rate}
+            for name, exec_, w, mb in (("plain", "plain", 1, 1), ("batched", "persistent", 2, 64)):
+                lat, span, mean_batch = run_serving(ctx, native, queries, arr, exec_, w, mb)
+                row[name] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                             "mean_ms": float(lat.mean()), "points_per_s": total_pts / span,
+                             "queries_per_s": len(queries) / span, "mean_batch_queries": mean_batch}
+            loads.append(row)
         # saturation throughput of the batching loop (all queries at once)
         _, span_b, mb_sat = run_serving(ctx, native, queries, None, "persistent", 2, 64)
-        res["saturation"] = {"plain_points_per_s": total_pts / span_cap, "batched_points_per_s": total_pts / span_b,
-                             "batched_mean_batch_queries": mb_sat}
-        res["trace"] = (f"{len(queries)} queries of the 10,000-query serving trace (seed {SERVE_SEED}): "
-                        "anticorrelated or independent FP32, N log-uniform in [1e3, 1e6], d uniform in 3..8, "
-                        "Sliced p = clamp(N / 8192, 1, 64); Poisson arrivals at 0.8 x the measured capacity of "
-                        "the plain path")
-        res["offered_queries_per_s"] = rate
-        res["points"] = total_pts
+        res = {"loads": loads,
+               "saturation": {"plain_points_per_s": total_pts / span_cap, "batched_points_per_s": total_pts / span_b,
+                              "batched_mean_batch_queries": mb_sat},
+               "plain_capacity_queries_per_s": cap_qps,
+               "trace": (f"{len(queries)} queries of the 10,000-query serving trace (seed {SERVE_SEED}): "
+                         "anticorrelated or independent FP32, N log-uniform in [1e3, 1e6], d uniform in 3..8, "
+                         "Sliced p = clamp(N / 8192, 1, 64), each a window of a seeded 2^20-row pool of its kind "
+                         "and d; Poisson arrivals at 0.5, 0.8 and 1.25 x the measured capacity of the plain path "
+                         "(the same arrival trace for both paths at each load)"),
+               "points": total_pts}
         return res
     finally:
         ctx.close()
+
+
+def serving_summary(serving):
+    """p99 latency (ms) of both paths at each offered load."""
+    if not serving:
+        return None
+    return {f"{row['load']}x": {"plain": round(row["plain"]["p99_ms"], 2),
+                                 "batched": round(row["batched"]["p99_ms"], 2),
+                                 "batched_mean_batch": round(row["batched"]["mean_batch_queries"], 2)}
+            for row in serving["loads"]}
 
 
 def gpu_arm(args, rank, world, local):
@@ -439,17 +459,44 @@ def gpu_arm(args, rank, world, local):
     e2e_value = pts_per_step * k_e2e * world / e2e_s
 
     # roofline of the dominance kernel (k_engine): algorithmic compares
-    # (oracle test count x d) over its measured launch time
+    # (oracle test count x d) over its measured launch time, against three
+    # denominators: the derived FP32-compare peak (SMs x 64 compare lanes x
+    # the maximum SM clock), the library's compare-rate probe (measured on
+    # this GPU), and the ceiling of the instruction the hot loop actually
+    # issues (sub.rn.f16x2 on the 128-lane FMA pipe: one attribute of two
+    # tests per lane per clock)
     wc = load_workcounts()
     roof = None
     dom_ms_per_step = acc["dom_ms"] / args.steps
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_ghz = (clk.get("sm_max_mhz") or 2070.0) / 1e3
+    probe_tcmp = None
+    try:
+        rate, _ = ctx.probe_compare_rate()
+        probe_tcmp = rate / 1e12
+    except native.SkylineError:
+        pass
     if wc:
-        tests = sum(wc[name]["local_tests"] + wc[name]["merge_tests"] for name in names)
+        loc_ms = statistics.mean(st["ms_dom_local"] for st in acc["stats"])
+        mer_ms = statistics.mean(st["ms_dom_merge"] for st in acc["stats"])
+        t_loc = sum(wc[name]["local_tests"] for name in names)
+        t_mer = sum(wc[name]["merge_tests"] for name in names)
+        tests = t_loc + t_mer
         achieved = tests * D / (dom_ms_per_step * 1e-3) / 1e12
-        peak = args.compare_peak_tcmp
+        peak = args.compare_peak_tcmp or sms * 64 * clk_ghz / 1e3
+        f16 = sms * 128 * 2 * clk_ghz / 1e3
+        a_loc = t_loc * D / (loc_ms * 1e-3) / 1e12
+        a_mer = t_mer * D / (mer_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": "k_engine (local + merge launches of the batched step)",
                 "achieved": achieved, "peak": peak, "unit": "Tcmp/s", "frac": achieved / peak,
-                "peak_source": "derived: 152 SMs x 64 FP32 compares/clk x 2.07 GHz",
+                "peak_source": f"derived: {sms} SMs x 64 FP32 compares/clk x {clk_ghz:.3f} GHz (max SM clock seen)",
+                "peak_probe": probe_tcmp, "frac_probe": achieved / probe_tcmp if probe_tcmp else None,
+                "f16x2_pipe_ceiling": f16, "frac_f16x2_pipe": achieved / f16,
+                "f16x2_source": f"{sms} SMs x 128 FMA lanes x 2 dim-compares per sub.rn.f16x2 x {clk_ghz:.3f} GHz",
+                "local": {"achieved": a_loc, "frac": a_loc / peak, "frac_f16x2_pipe": a_loc / f16,
+                          "ms": loc_ms, "algorithmic_tests": t_loc},
+                "merge": {"achieved": a_mer, "frac": a_mer / peak, "frac_f16x2_pipe": a_mer / f16,
+                          "ms": mer_ms, "algorithmic_tests": t_mer},
                 "traffic": engine_traffic(), "traffic_unit": "DRAM bytes per step (ncu, both engine launches)",
                 "algorithmic_tests_per_step": tests,
                 "kernel_ms_per_step": dom_ms_per_step,
@@ -476,7 +523,7 @@ def gpu_arm(args, rank, world, local):
 
     serving = None
     if rank == 0 and not args.no_serving:
-        serving = serving_leg(native, local)
+        serving = serving_leg(native, local, args.serve_queries)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -504,7 +551,12 @@ def gpu_arm(args, rank, world, local):
                        "exec": "batched: the 4 queries in one call, all local skylines in one persistent launch, "
                                "all merges in a second",
                        "l2": "flushed between timed steps (256 MB write outside the timed events)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       # the batched-vs-plain comparison of the metric, kept beside the headline
+                       "plain_points_per_s": plain_value,
+                       "speedup_batched_over_plain": value / plain_value,
+                       "graph_points_per_s": graph["value"] if graph else None,
+                       "serving_p99_ms": serving_summary(serving)},
             "graph": graph,
             "per_query_persistent": {"value": pq_value, "unit": "points/s",
                                      "ms_per_step": sum(ms_pq) / len(ms_pq)},
@@ -705,9 +757,10 @@ def main():
     ap.add_argument("--ncu-case", choices=["small", "batch"], default=None,
                     help="run a profiling case only, twice, default knobs, no timing: 'small' = one query "
                          "(anticorrelated N=200k, d=6, Sliced p=64); 'batch' = the benchmark's batched step")
-    # FP32 compare peak: 152 SMs x 64 compare lanes per SM per clock x 2.07 GHz
-    # (the compare-rate probe of the library measures 58.6 per SM per clock)
-    ap.add_argument("--compare-peak-tcmp", type=float, default=SM_COUNT * 64 * 2.07e9 / 1e12)
+    # FP32 compare peak in T compares/s; 0 derives it from the device's SM
+    # count x 64 compare lanes per SM per clock x the maximum SM clock seen
+    ap.add_argument("--compare-peak-tcmp", type=float, default=0.0)
+    ap.add_argument("--serve-queries", type=int, default=SERVE_QUERIES)
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.ncu_case:
