@@ -94,12 +94,12 @@ typedef struct {
   uint32_t dom_block;          /* dominator block per work item (points, multiple of 32, <= 2048; default 1024) */
 } sky_params;
 
-/* Per-call statistics (the last sky_skyline call of the context). */
+/* Per-call statistics (sky_get_stats). */
 typedef struct {
   uint64_t n;                  /* input points */
   uint32_t d;
   uint32_t partitions;         /* p after clamping */
-  uint32_t nonempty_partitions;
+  uint32_t nonempty_partitions; /* partitions holding at least one point (before Grid Filtering) */
   uint32_t rounds_local;       /* SFS rounds of the local phase (max over partitions) */
   uint32_t rounds_merge;       /* SFS rounds of the sequential merge */
   uint32_t reps_kept;          /* representatives left after removing dominated ones */
@@ -283,8 +283,17 @@ sky_status sky_wait(sky_ctx* ctx, uint64_t ticket, uint32_t* out_idx, uint64_t* 
    workspaces are freed).  Uncollected tickets stay collectable. */
 sky_status sky_serve_stop(sky_ctx* ctx);
 
-/* Statistics of the last completed call. */
-sky_status sky_get_stats(sky_ctx* ctx, sky_stats* out);
+/* Statistics of a call.  ticket_or_0 = 0: the last completed sky_skyline,
+   sky_skyline_ex or sky_skyline_batch call of the context (a batch's sizes
+   and counts are sums over its queries, its round counts maxima).  A
+   serving ticket: that query's own sizes and counts (Section 3 partitions,
+   filtered points, |u|, |Sky|), with the launches and device times of the
+   batch it ran in (device times only when sky_set_timing was on when the
+   serving loop started); available from completion until long after
+   sky_wait collects the ticket (the last 4096 collected tickets are kept).
+   SKY_EBUSY if the ticket has not completed, SKY_ECANCELLED if it is
+   unknown, SKY_EINVAL for NULL arguments. */
+sky_status sky_get_stats(sky_ctx* ctx, uint64_t ticket_or_0, sky_stats* out);
 
 /* Text of a status code (static storage). */
 const char* sky_status_str(sky_status s);
@@ -307,20 +316,23 @@ void sky_destroy(sky_ctx* ctx);
    one file-scope device array of the library, reserved on every GPU that
    loads the library until the process exits.
 
-   Sky(points) (Def. 1) of a small point set: points is device memory of the
-   current device, row-major N x d FP32, read-only; out_idx is device memory
-   of capacity >= N and receives the |Sky| ascending indices; *out_count
-   (host) receives |Sky|.  The work runs on cuda_stream (NULL = legacy
-   default stream) and the call blocks until it is done.  Errors:
-   SKY_EINVAL for d outside 1..8, N > SKY_STATIC_MAX_POINTS, NULL or host
-   pointers, or a NaN attribute; SKY_ECUDA if a CUDA call fails.  N = 0
-   returns SKY_OK with count 0.  The result equals sky_skyline's.
+   The skyline of a small point set, the same set sky_skyline returns:
+   points is device memory of the current device (or managed memory),
+   row-major N x d FP32, read-only; out_idx is device memory of the current
+   device of capacity >= N and receives the |Sky| ascending indices;
+   *out_count (host) receives |Sky|.  The work runs on cuda_stream (NULL =
+   legacy default stream); the call copies the count to the host and waits
+   for the stream before it returns.  Errors: SKY_EINVAL for d outside 1..8,
+   N > SKY_STATIC_MAX_POINTS, NULL pointers, host memory or memory of
+   another GPU, or a NaN attribute; SKY_ECUDA if a CUDA call fails.  N = 0
+   returns SKY_OK with count 0.
 
    The first call on a device looks up the array's device address on that
    device (the current one) and caches it, so it should come before any
-   stream capture.  Every call reuses the same array, so calls whose work
-   overlaps on the GPU -- from several host threads or on several streams
-   at once -- race and must not be made. */
+   stream capture; after a cudaDeviceReset the next call looks it up again.
+   Every call reuses the same array, so calls whose work overlaps on the
+   GPU -- from several host threads or on several streams at once -- race
+   and must not be made. */
 sky_status sky_skyline_static(const float* points, uint64_t n, uint32_t d, uint32_t* out_idx,
                               uint64_t* out_count, void* cuda_stream);
 

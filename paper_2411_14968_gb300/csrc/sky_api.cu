@@ -152,7 +152,7 @@ sky_status serve_start_locked(sky_ctx* ctx, const sky_serve_config* cfg) {
   if (!ctx->server) ctx->server.reset(new Server());
   if (ctx->server->running()) return SKY_EBUSY;
   std::string msg;
-  sky_status s = ctx->server->start(ctx->run.device, cfg ? *cfg : def, &msg);
+  sky_status s = ctx->server->start(ctx->run.device, cfg ? *cfg : def, ctx->run.timing, &msg);
   if (s != SKY_OK) {
     ctx->server->shutdown();
     ctx->serve_error = msg.empty() ? "serving start failed" : msg;
@@ -275,10 +275,19 @@ void sky_graph_destroy(sky_graph* graph) {
   delete graph;
 }
 
-sky_status sky_get_stats(sky_ctx* ctx, sky_stats* out) {
+sky_status sky_get_stats(sky_ctx* ctx, uint64_t ticket_or_0, sky_stats* out) {
   if (!ctx || !out) return SKY_EINVAL;
-  *out = ctx->run.stats;
-  return SKY_OK;
+  if (ticket_or_0 == 0) {
+    *out = ctx->run.stats;
+    return SKY_OK;
+  }
+  Server* srv = nullptr;
+  {
+    std::lock_guard<std::mutex> g(ctx->serve_mu);
+    srv = ctx->server.get();
+  }
+  if (!srv) return SKY_ECANCELLED;
+  return srv->stats(ticket_or_0, out);
 }
 
 const char* sky_status_str(sky_status s) {
@@ -309,6 +318,13 @@ sky_status sky_probe_compare_rate(sky_ctx* ctx, uint32_t iterations, double* com
     ctx->run.last_error = std::string("compare probe: ") + cudaGetErrorString(e);
     return SKY_ECUDA;
   }
+  return SKY_OK;
+}
+
+sky_status sky_diag_engine_wait_test(sky_ctx* ctx, uint64_t wait_limit_ns, uint32_t withhold_task) {
+  if (!ctx || wait_limit_ns < 1000000ull) return SKY_EINVAL;
+  ctx->run.test_wait_ns = wait_limit_ns;
+  ctx->run.test_withhold_task = withhold_task;
   return SKY_OK;
 }
 

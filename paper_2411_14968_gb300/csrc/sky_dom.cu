@@ -272,9 +272,10 @@ __global__ void k_noseq_groups(const u32* __restrict__ useg, u32 P, u32* __restr
 // partitions removed by Grid Filtering get no work.  Every per-point array
 // of a segment is the slice [seg_off[s], seg_off[s + 1]) of the whole array.
 __global__ void k_build_segs(const u32* __restrict__ seg_off, u32 P, const u8* __restrict__ dropped, SegArrays a,
-                             int d, SegDesc* segs) {
+                             int d, SegDesc* segs, u32* nonempty) {
   u64 s = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= P) return;
+  if (nonempty && seg_off[s + 1] > seg_off[s]) atomicAdd(nonempty, 1u);
   const int V = vec_of(d);
   u32 o = seg_off[s];
   SegDesc sd;
@@ -316,10 +317,10 @@ int g_sm_count = 0;
 }  // namespace
 
 cudaError_t launch_build_segs(const u32* seg_off, u32 P, const u8* dropped, const SegArrays& a, int d,
-                              SegDesc* segs, cudaStream_t st) {
+                              SegDesc* segs, u32* nonempty, cudaStream_t st) {
   if (P == 0) return cudaSuccess;
   note_launch();
-  k_build_segs<<<(P + 255) / 256, 256, 0, st>>>(seg_off, P, dropped, a, d, segs);
+  k_build_segs<<<(P + 255) / 256, 256, 0, st>>>(seg_off, P, dropped, a, d, segs, nonempty);
   return cudaGetLastError();
 }
 

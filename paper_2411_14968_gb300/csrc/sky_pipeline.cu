@@ -119,7 +119,7 @@ constexpr u32 ORDERED_MAX_SEGS = 8;
 
 // word slots of Bufs::words
 enum { W_ERR = 0, W_COLMAX = 1, W_GRID_DROPPED = 9, W_KEPT = 10, W_NU = 11, W_SKY = 12, W_MAXROUND_LOCAL = 13,
-       W_MAXROUND_MERGE = 14, W_HIST = 16, W_NOSEQ_CTR = 24, W_WORDS = 32 };
+       W_MAXROUND_MERGE = 14, W_NONEMPTY = 15, W_HIST = 16, W_NOSEQ_CTR = 24, W_WORDS = 32 };
 
 size_t layout(const Plan& pl, u32 ang_words, Carve& c, Bufs* b) {
   const size_t start = c.off;
@@ -335,14 +335,20 @@ sky_status validate_query(const float* points, u64 n, u32 d, const sky_params* p
   return validate(points, n, d, params, &pl, msg);
 }
 
-bool is_device_ptr(const void* p) {
+int pointer_kind(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return PTR_HOST;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return PTR_DEVICE;
+  if (a.type != cudaMemoryTypeDevice) return PTR_HOST;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return PTR_OTHER_DEVICE;
+  return a.device == cur ? PTR_DEVICE : PTR_OTHER_DEVICE;
 }
+
+bool is_device_ptr(const void* p) { return pointer_kind(p) == PTR_DEVICE; }
 
 Runner::~Runner() {
   if (ws_ || pinned_ || ev_[0]) {
@@ -447,9 +453,11 @@ size_t Runner::query_bytes(u64 n, u32 d, const sky_params* params) {
 sky_status Runner::run(Query* queries, u32 nq) {
   BatchState B;
   sky_status s = prepare(B, queries, nq, false);
+  if (s == SKY_OK && !B.empty) s = enqueue(B);
+  // the wait-test hooks apply to one call
+  test_wait_ns = 0;
+  test_withhold_task = 0;
   if (s != SKY_OK || B.empty) return s;
-  s = enqueue(B);
-  if (s != SKY_OK) return s;
   return finish(B);
 }
 
@@ -491,6 +499,13 @@ sky_status Runner::prepare(BatchState& B, Query* queries, u32 nq, bool graph) {
     q.stats.d = q.d;
     q.stats.partitions = w.pl.P;
     if (q.n == 0) continue;
+    if (pointer_kind(q.points) == PTR_OTHER_DEVICE || pointer_kind(q.out_idx) == PTR_OTHER_DEVICE ||
+        (q.out_pid && pointer_kind(q.out_pid) == PTR_OTHER_DEVICE) ||
+        (q.out_stage && pointer_kind(q.out_stage) == PTR_OTHER_DEVICE)) {
+      q.status = SKY_EINVAL;
+      return fail(SKY_EINVAL, (nq > 1 ? "query " + std::to_string(i) + ": " : std::string()) +
+                                  "a buffer is device memory of another GPU than the context's");
+    }
     w.pl.x_on_host = !is_device_ptr(q.points);
     w.out_dev = is_device_ptr(q.out_idx);
     w.pid_dev = q.out_pid && is_device_ptr(q.out_pid);
@@ -710,7 +725,7 @@ sky_status Runner::enqueue(BatchState& B) {
       CK(launch_stamp_stage(b.alive, n, b.stage_s, ST_REP, st));
     }
     SegArrays sa{b.pts, b.hc, b.score, b.alive, b.win, b.whc, b.dpos, b.dhc};
-    CK(launch_build_segs(b.seg_off, P, w.dropped, sa, D, bb.segs + w.seg_base, st));
+    CK(launch_build_segs(b.seg_off, P, w.dropped, sa, D, bb.segs + w.seg_base, b.words + W_NONEMPTY, st));
   }
   CK(join());
   record(3, B);
@@ -730,6 +745,8 @@ sky_status Runner::enqueue(BatchState& B) {
   auto engine = [&](const SegDesc* segs, u32 nseg, EngineCfg cfg, u32* err, u32* round_dst,
                     u32 ordered) -> cudaError_t {
     cfg.ordered = ordered;
+    cfg.wait_ns = test_wait_ns;
+    cfg.withhold_task = test_withhold_task;
     cudaError_t e = cudaMemsetAsync(bb.tdoneA, 0, bb.tcap * sizeof(u32), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(bb.tdoneB, 0, bb.tcap * sizeof(u32), st);
     if (e != cudaSuccess) return e;
@@ -949,6 +966,7 @@ sky_status Runner::finish(BatchState& B) {
     S.rounds_local = shared ? shared_round_local : w.words[W_MAXROUND_LOCAL];
     S.rounds_merge = (shared && w.mseg >= 0) ? shared_round_merge : w.words[W_MAXROUND_MERGE];
     S.reps_kept = w.pl.rep ? w.words[W_KEPT] : 0;
+    S.nonempty_partitions = w.words[W_NONEMPTY];
     S.grid_dropped = w.words[W_HIST + ST_GRID];
     S.rep_dropped = w.words[W_HIST + ST_REP];
     S.local_union = (u64)w.words[W_HIST + ST_MERGE] + w.words[W_HIST + ST_SKY];
@@ -962,6 +980,7 @@ sky_status Runner::finish(BatchState& B) {
     stats.n += S.n;
     stats.d = std::max(stats.d, S.d);
     stats.partitions += S.partitions;
+    stats.nonempty_partitions += S.nonempty_partitions;
     stats.rounds_local = std::max(stats.rounds_local, S.rounds_local);
     stats.rounds_merge = std::max(stats.rounds_merge, S.rounds_merge);
     stats.reps_kept += S.reps_kept;

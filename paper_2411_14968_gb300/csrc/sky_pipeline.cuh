@@ -36,6 +36,10 @@ class Runner {
   std::string last_error;
   sky_stats stats{};
   EngineGate* gate = nullptr;   // set when several Runners share the device
+  // Test hooks of the engine's bounded waits for the next run() only
+  // (EngineCfg::wait_ns, EngineCfg::withhold_task); zero = off.
+  u64 test_wait_ns = 0;
+  u32 test_withhold_task = 0;
 
   ~Runner();
   sky_status init(int dev, size_t mem_budget);
@@ -94,7 +98,13 @@ class Runner {
   void record(int i, const BatchState& B);
 };
 
-bool is_device_ptr(const void* p);
+// Where a caller's pointer lives: host memory (pageable, pinned or unknown
+// to CUDA), device memory of the current device (or managed memory), or
+// device memory of another device, which the library's kernels must not be
+// given.
+enum { PTR_HOST = 0, PTR_DEVICE = 1, PTR_OTHER_DEVICE = 2 };
+int pointer_kind(const void* p);
+bool is_device_ptr(const void* p);  // pointer_kind(p) == PTR_DEVICE
 
 // A batch captured into a CUDA graph with its own Runner (workspace, pinned
 // staging, stream), replayed as one graph launch.  Inputs and outputs must

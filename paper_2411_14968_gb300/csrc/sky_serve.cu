@@ -42,8 +42,12 @@ struct Server::Ticket {
   sky_status status = SKY_OK;
   bool done = false;
   u32 batch_queries = 0;
+  sky_stats stats{};
   Clock::time_point t_submit, t_start, t_done;
 };
+
+// Statistics of collected tickets kept for sky_get_stats (the most recent).
+constexpr size_t KEEP_COLLECTED_STATS = 4096;
 
 struct Server::Impl {
   int device = 0;
@@ -60,6 +64,7 @@ struct Server::Impl {
   bool stop = false;
   u64 next_id = 1;
   u64 batches = 0;
+  std::deque<std::pair<u64, sky_stats>> collected;  // (ticket, statistics), oldest first
 
   void loop(u32 w);
 };
@@ -68,7 +73,7 @@ Server::Server() : impl_(new Impl) {}
 
 Server::~Server() { shutdown(); }
 
-sky_status Server::start(int device, const sky_serve_config& cfg, std::string* msg) {
+sky_status Server::start(int device, const sky_serve_config& cfg, int timing, std::string* msg) {
   Impl& I = *impl_;
   I.device = device;
   const u32 nw = cfg.workers ? cfg.workers : 2;
@@ -97,6 +102,7 @@ sky_status Server::start(int device, const sky_serve_config& cfg, std::string* m
     sky_status st = r->init(device, I.budget_per_worker);
     if (st != SKY_OK) return st;
     r->stream = s;
+    r->timing = timing;
     r->gate = nw > 1 ? &I.gate : nullptr;
     I.runners.push_back(std::move(r));
   }
@@ -179,6 +185,14 @@ void Server::Impl::loop(u32 w) {
         if (t->status != SKY_OK) t->count = 0;
         t->result.resize(t->count);
         t->batch_queries = (u32)batch.size();
+        // the query's own sizes and counts; launches and device times are
+        // those of its whole batch (the batch shares its engine launches)
+        t->stats = qs[i].stats;
+        t->stats.launches = R.stats.launches;
+        t->stats.ms_total = R.stats.ms_total;
+        for (int k = 0; k < 6; ++k) t->stats.ms_phase[k] = R.stats.ms_phase[k];
+        t->stats.ms_dom_local = R.stats.ms_dom_local;
+        t->stats.ms_dom_merge = R.stats.ms_dom_merge;
         t->t_done = t1;
         t->done = true;
       }
@@ -244,6 +258,8 @@ sky_status Server::wait(u64 ticket, u32* out_idx, u64* out_count, int64_t timeou
     }
     t = std::move(it->second);
     I.tickets.erase(it);
+    I.collected.emplace_back(t->id, t->stats);
+    if (I.collected.size() > KEEP_COLLECTED_STATS) I.collected.pop_front();
   }
   if (info) {
     info->queue_us = us_between(t->t_submit, t->t_start);
@@ -265,6 +281,24 @@ sky_status Server::wait(u64 ticket, u32* out_idx, u64* out_count, int64_t timeou
     }
   }
   return SKY_OK;
+}
+
+sky_status Server::stats(u64 ticket, sky_stats* out) {
+  Impl& I = *impl_;
+  std::lock_guard<std::mutex> g(I.mu);
+  auto it = I.tickets.find(ticket);
+  if (it != I.tickets.end()) {
+    if (!it->second->done) return SKY_EBUSY;
+    *out = it->second->stats;
+    return SKY_OK;
+  }
+  for (auto c = I.collected.rbegin(); c != I.collected.rend(); ++c) {
+    if (c->first == ticket) {
+      *out = c->second;
+      return SKY_OK;
+    }
+  }
+  return SKY_ECANCELLED;
 }
 
 u64 Server::batches() const {

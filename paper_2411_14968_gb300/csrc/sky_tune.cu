@@ -97,7 +97,7 @@ sky_status tune(sky_ctx* ctx, const sky_query* queries, uint32_t nq, uint32_t ma
     sky_status s = sky_skyline_batch(ctx, qs.data(), nq);
     if (s != SKY_OK) return s;
     sky_stats st;
-    sky_get_stats(ctx, &st);
+    sky_get_stats(ctx, 0, &st);
     *ms = st.ms_total;
     return SKY_OK;
   };

@@ -105,7 +105,7 @@ EXPORTS = ["sky_params_init", "sky_create", "sky_set_stream", "sky_set_timing", 
            "sky_skyline_ex", "sky_get_stats", "sky_status_str", "sky_last_error", "sky_destroy",
            "sky_probe_compare_rate", "sky_skyline_static", "sky_skyline_batch", "sky_serve_config_init", "sky_query_bytes",
            "sky_serve_start", "sky_submit", "sky_poll", "sky_wait", "sky_serve_stop", "sky_autotune", "sky_autotune_batch",
-           "sky_graph_capture", "sky_graph_launch", "sky_graph_destroy"]
+           "sky_graph_capture", "sky_graph_launch", "sky_graph_destroy", "sky_diag_engine_wait_test"]
 
 _lock = threading.Lock()
 _lib = None
@@ -144,7 +144,7 @@ def load(build_if_missing: bool = True):
         L.sky_skyline.restype = i32
         L.sky_skyline_ex.argtypes = [P, P, u64, u32, ctypes.POINTER(SkyParams), P, ctypes.POINTER(u64), P, P]
         L.sky_skyline_ex.restype = i32
-        L.sky_get_stats.argtypes = [P, ctypes.POINTER(SkyStats)]
+        L.sky_get_stats.argtypes = [P, u64, ctypes.POINTER(SkyStats)]
         L.sky_get_stats.restype = i32
         L.sky_status_str.argtypes = [i32]
         L.sky_status_str.restype = ctypes.c_char_p
@@ -182,6 +182,8 @@ def load(build_if_missing: bool = True):
         L.sky_serve_stop.argtypes = [P]
         L.sky_serve_stop.restype = i32
         L.sky_skyline_static.argtypes = [P, u64, u32, P, ctypes.POINTER(u64), P]
+        L.sky_diag_engine_wait_test.argtypes = [P, u64, u32]
+        L.sky_diag_engine_wait_test.restype = i32
         L.sky_skyline_static.restype = i32
         _lib = L
         return L
@@ -261,9 +263,17 @@ class Context:
         self._check(self._L.sky_probe_compare_rate(self._h, int(iterations), ctypes.byref(rate), ctypes.byref(sms)))
         return rate.value, sms.value
 
-    def stats(self) -> dict:
+    def engine_wait_test(self, wait_limit_ns: int, withhold_task: int):
+        """Arms the next skyline call's test hook of the engine's bounded
+        waits (sky_diag_engine_wait_test): waits give up after wait_limit_ns
+        without progress, and the withhold_task-th task an engine launch
+        publishes is never marked published (0 = none)."""
+        self._check(self._L.sky_diag_engine_wait_test(self._h, int(wait_limit_ns), int(withhold_task)))
+
+    def stats(self, ticket: int = 0) -> dict:
+        """Statistics of the last call (ticket 0) or of a serving ticket."""
         s = SkyStats()
-        self._check(self._L.sky_get_stats(self._h, ctypes.byref(s)))
+        self._check(self._L.sky_get_stats(self._h, int(ticket), ctypes.byref(s)))
         return s.as_dict()
 
     def skyline(self, points, params: SkyParams | None = None, out=None, with_diag: bool = False, **kw):

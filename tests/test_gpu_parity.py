@@ -42,6 +42,10 @@ def _check(ctx, oracle_mod, x, scheme="none", p=1, slices=None, normalize=False,
     np.testing.assert_array_equal(idx, want["indices"], err_msg=tag)
     np.testing.assert_array_equal(pid, want["pid"], err_msg=tag + " pid")
     np.testing.assert_array_equal(stage, want["stage"], err_msg=tag + " stage")
+    if x.shape[0]:
+        st = ctx.stats()
+        assert st["nonempty_partitions"] == np.unique(want["pid"]).shape[0], tag
+        assert st["skyline"] == want["indices"].shape[0], tag
     return idx
 
 

@@ -127,3 +127,34 @@ def test_errors_are_per_ticket(native_mod):
         with pytest.raises(native.SkylineError):
             ctx.submit(np.zeros((5, 9), np.float32))
         ctx.serve_stop()
+
+
+def test_per_ticket_statistics(native_mod):
+    # sky_get_stats(ctx, ticket, ...): a served query's own sizes and counts,
+    # equal to what the same query reports when run alone
+    native = native_mod
+    qs = _trace(native, 12, 7)
+    alone = []
+    with native.Context(0) as ctx:
+        for x, p in qs:
+            r = ctx.skyline(x, params=p)
+            alone.append((r, ctx.stats()))
+    with native.Context(0) as ctx:
+        ctx.set_timing(True)
+        ctx.serve_start(workers=2, max_batch=4)
+        tickets = [ctx.submit(x, p) for x, p in qs]
+        for i, t in enumerate(tickets):
+            got, info = ctx.wait(t)
+            st = ctx.stats(t)  # still available after the ticket is collected
+            want, ws = alone[i]
+            np.testing.assert_array_equal(got, want)
+            assert st["n"] == qs[i][0].shape[0] and st["d"] == qs[i][0].shape[1]
+            assert st["skyline"] == want.shape[0]
+            for key in ("partitions", "nonempty_partitions", "local_union", "rep_dropped", "grid_dropped",
+                        "reps_kept"):
+                assert st[key] == ws[key], (i, key)
+            assert st["launches"] > 0 and st["ms_total"] > 0
+        with pytest.raises(native.SkylineError) as e:
+            ctx.stats(tickets[-1] + 1000)
+        assert e.value.status == native.SKY_ECANCELLED
+        ctx.serve_stop()
