@@ -721,6 +721,35 @@ def configs_experiment(local: int):
     print(json.dumps({"experiment": "workload configurations", "rows": out}), flush=True)
 
 
+def shapes_experiment(local: int):
+    """The batched step (the benchmark's four queries as one batch) with each
+    compiled launch shape of the engine -- warps per CTA x candidates per
+    lane, i.e. the tile width of a work item -- at the default chunk and
+    block knobs: device time of the whole batch and of its two engine
+    launches (median of 7 runs, CUDA events)."""
+    import torch
+    from paper_2411_14968_gb300 import datagen, native
+    x = datagen.anticorrelated(N, D, SEED)
+    xt = torch.from_numpy(x).cuda()
+    rows = []
+    with native.Context(local) as ctx:
+        ctx.set_timing(True)
+        for w, r in ((4, 4), (8, 4), (4, 2), (8, 2)):
+            ps = [native.make_params(engine_warps=w, engine_cands=r, **kw) for _, kw in VARIANTS]
+            for _ in range(2):
+                ctx.skyline_batch([(xt, p) for p in ps])
+            sts = []
+            for _ in range(7):
+                ctx.skyline_batch([(xt, p) for p in ps])
+                sts.append(ctx.stats())
+            med = lambda k: statistics.median(st[k] for st in sts)  # noqa: E731
+            rows.append({"warps": w, "cands_per_lane": r, "tile": 32 * w * r, "ms_total": round(med("ms_total"), 3),
+                         "ms_dom_local": round(med("ms_dom_local"), 3), "ms_dom_merge": round(med("ms_dom_merge"), 3),
+                         "points_per_s": len(VARIANTS) * N / (med("ms_total") * 1e-3)})
+            print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"experiment": "engine launch shapes on the batched step", "rows": rows}), flush=True)
+
+
 def ncu_case(which: str):
     """The cases the engine's ncu captures run: the two k_engine launches
     (local phase, merge) of the second call are the captured ones."""
@@ -752,7 +781,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--experiment", choices=["rep-filtering", "sweeps", "configs"], default=None,
+    ap.add_argument("--experiment", choices=["rep-filtering", "sweeps", "configs", "shapes"], default=None,
                     help="run one of the paper's experiments instead of the benchmark")
     ap.add_argument("--ncu-case", choices=["small", "batch"], default=None,
                     help="run a profiling case only, twice, default knobs, no timing: 'small' = one query "
@@ -774,6 +803,9 @@ def main():
         return
     if args.experiment == "configs":
         configs_experiment(local)
+        return
+    if args.experiment == "shapes":
+        shapes_experiment(local)
         return
     if args.impl == "reference":
         reference_arm(args, rank, world)

@@ -92,6 +92,9 @@ typedef struct {
   uint32_t chunk_max;          /* largest SFS chunk of a partition (points; default 262144) */
   uint32_t chunk_alpha_x4;     /* next chunk = alpha/4 x current window size, clamped (default 32) */
   uint32_t dom_block;          /* dominator block per work item (points, multiple of 32, <= 2048; default 1024) */
+  uint32_t engine_warps;       /* warps per CTA of the engine's work items: 4 or 8 (default 4) */
+  uint32_t engine_cands;       /* candidates per lane: 2 or 4 (default 4); a work item's tile is
+                                  32 x engine_warps x engine_cands candidates */
 } sky_params;
 
 /* Per-call statistics (sky_get_stats). */
@@ -176,9 +179,12 @@ typedef struct {
 sky_status sky_skyline_batch(sky_ctx* ctx, sky_query* queries, uint32_t nq);
 
 /* Autotuner of the dominance engine's knobs (chunk_min, chunk_max,
-   chunk_alpha_x4, dom_block of sky_params): the SFS chunk sizes of the
-   engine's rounds and the dominator block a CTA stages in shared memory.
-   They decide how Algorithm 1 is cut into parallel work, never the result.
+   chunk_alpha_x4, dom_block, engine_warps, engine_cands of sky_params):
+   the SFS chunk sizes of the engine's rounds, the dominator block a CTA
+   stages in shared memory, and the launch shape (warps per CTA and
+   candidates per lane, i.e. the tile width of a work item and the warps
+   that share a partition's tile).  They decide how Algorithm 1 is cut into
+   parallel work, never the result.
    Runs the query (points, n, d with the method parameters in *params) up
    to max_trials times (0 = 48) with candidate knobs, timing each run with
    CUDA events on the context's stream (coordinate descent from the
@@ -192,7 +198,7 @@ sky_status sky_autotune(sky_ctx* ctx, const float* points, uint64_t n, uint32_t 
    all queries (the queries share the engine's launches, so the best knobs
    of a batch differ from those of its queries alone).  queries[i].params
    hold the method parameters (their knobs are ignored); out_idx and
-   out_count of the queries are not used.  The four knob fields of *knobs
+   out_count of the queries are not used.  The six knob fields of *knobs
    (struct_size set, e.g. by sky_params_init) receive the result. */
 sky_status sky_autotune_batch(sky_ctx* ctx, const sky_query* queries, uint32_t nq, uint32_t max_trials,
                               sky_params* knobs, double* best_ms);

@@ -19,7 +19,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libskyline.so")
-SOURCES = ["sky_api.cu", "sky_dom.cu", "sky_engine.cu", "sky_prep.cu", "sky_pipeline.cu", "sky_prims.cu", "sky_probe.cu",
+SOURCES = ["sky_engine_w4r4.cu", "sky_engine_w8r4.cu", "sky_engine_w4r2.cu", "sky_engine_w8r2.cu", "sky_api.cu",
+           "sky_dom.cu", "sky_engine.cu", "sky_prep.cu", "sky_pipeline.cu", "sky_prims.cu", "sky_probe.cu",
            "sky_serve.cu", "sky_static.cu", "sky_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC,-O2",
@@ -36,6 +37,7 @@ def nvcc() -> str:
 def _inputs():
     deps = [os.path.join(CSRC, s) for s in SOURCES]
     deps += [os.path.join(CSRC, "sky_internal.cuh"), os.path.join(CSRC, "sky_pipeline.cuh"),
+             os.path.join(CSRC, "sky_engine_impl.cuh"),
              os.path.join(CSRC, "sky_serve.cuh"), os.path.join(ROOT, "include", "skyline.h"),
              os.path.join(ROOT, "include", "skyline_diag.h"),
              os.path.abspath(__file__)]

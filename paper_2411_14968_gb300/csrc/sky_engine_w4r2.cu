@@ -1,0 +1,5 @@
+// The persistent local-skyline engine with 4 warps per CTA and 2 candidates
+// per lane (tiles of 256 candidates); see sky_engine_impl.cuh.
+#define SKY_ENGINE_WARPS 4
+#define SKY_ENGINE_R 2
+#include "sky_engine_impl.cuh"

@@ -222,9 +222,18 @@ constexpr u32 DEFAULT_CHUNK_MIN = 1024;
 constexpr u32 DEFAULT_CHUNK_MAX = 262144;
 constexpr u32 DEFAULT_ALPHA_X4 = 32;
 constexpr u32 DEFAULT_DOM_BLOCK = 1024;
+// Default launch shape of the engine: warps per CTA x candidates per lane.
+constexpr u32 DEFAULT_ENGINE_WARPS = 4;
+constexpr u32 DEFAULT_ENGINE_CANDS = 4;
+// Smallest tile (candidates per work item) of any compiled shape: 4 warps x
+// 32 lanes x 2 candidates.
+constexpr u32 ENGINE_MIN_TILE = 256;
 
 struct EngineCfg {
   u32 chunk_min, chunk_max, alpha_x4, dom_block;
+  // launch shape: warps per CTA (4 or 8) and candidates per lane (2 or 4);
+  // 0 selects the default
+  u32 warps, cands;
   // 1: keep each segment's dense list in position order (look-back between
   // tiles) so phase B tests only the lower-score half of the dense square;
   // pays off for large chunks (the merge), costs waits for many small ones
@@ -263,6 +272,12 @@ u32 engine_max_dom_block();
 // points (alive = 0) and leaves each segment's skyline in its window.
 cudaError_t engine_run(const SegDesc* segs_dev, u32 nseg, const EngineCfg& cfg, const EngineWork& w, u32* err,
                        cudaStream_t st);
+// Whether (warps, cands) names a compiled launch shape (0 = default).
+bool engine_shape_ok(u32 warps, u32 cands);
+// engine_run for one compiled shape (sky_engine_w<W>r<R>.cu).
+template <int W, int RR>
+cudaError_t engine_run_variant(const SegDesc* segs_dev, u32 nseg, const EngineCfg& cfg, const EngineWork& w,
+                               u32* err, cudaStream_t st);
 
 // Segment descriptors (sky_dom.cu).
 struct SegArrays {

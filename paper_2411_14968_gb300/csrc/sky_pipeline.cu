@@ -270,6 +270,10 @@ sky_status validate(const float* points, u64 n, u32 d, const sky_params* pa, Pla
   if (pl->cfg.dom_block % 32) return bad("dom_block must be a multiple of 32");
   if (pl->cfg.dom_block > engine_max_dom_block()) return bad("dom_block above the engine's maximum");
   if (pl->cfg.chunk_min > (1u << 24) || pl->cfg.chunk_max > (1u << 24)) return bad("chunk too large");
+  if (!engine_shape_ok(p.engine_warps, p.engine_cands))
+    return bad("engine_warps must be 0, 4 or 8 and engine_cands 0, 2 or 4");
+  pl->cfg.warps = p.engine_warps ? p.engine_warps : DEFAULT_ENGINE_WARPS;
+  pl->cfg.cands = p.engine_cands ? p.engine_cands : DEFAULT_ENGINE_CANDS;
   return SKY_OK;
 }
 

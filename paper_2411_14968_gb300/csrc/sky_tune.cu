@@ -1,9 +1,10 @@
 // sky_autotune: picks the dominance engine's tuning knobs for a workload by
 // measurement.  The knobs change only how Algorithm 1 is cut into parallel
 // work (chunk sizes of the SFS rounds, the dominator block a CTA stages in
-// shared memory), never the result, so any choice is exact; the tuner
-// times whole queries (CUDA events around the call on the context's stream)
-// and keeps the fastest.
+// shared memory, the launch shape: warps per CTA and candidates per lane,
+// i.e. a work item's tile width), never the result, so any choice is exact;
+// the tuner times whole queries (CUDA events around the call on the
+// context's stream) and keeps the fastest.
 //
 // A batch is tuned as a whole (one set of knobs for all of its queries): the
 // best knobs for a batch differ from those of its queries alone, because
@@ -11,7 +12,8 @@
 //
 // Search: from the built-in defaults, a joint search over the chunk growth
 // factor and the first chunk length (the two knobs that interact most),
-// then coordinate descent: for each knob in turn every candidate value is
+// then every launch shape, then coordinate descent (the launch shape
+// counting as one knob): for each knob in turn every candidate value is
 // tried with the others held at their best values so far; two sweeps,
 // within a trial budget.  Each candidate runs three times and counts its
 // median run; the winner is then confirmed against the starting knobs by the
@@ -79,6 +81,10 @@ sky_status tune(sky_ctx* ctx, const sky_query* queries, uint32_t nq, uint32_t ma
   if (!cur.chunk_min) cur.chunk_min = sky::DEFAULT_CHUNK_MIN;
   if (!cur.chunk_max) cur.chunk_max = sky::DEFAULT_CHUNK_MAX;
   if (!cur.chunk_alpha_x4) cur.chunk_alpha_x4 = sky::DEFAULT_ALPHA_X4;
+  if (!cur.engine_warps) cur.engine_warps = sky::DEFAULT_ENGINE_WARPS;
+  if (!cur.engine_cands) cur.engine_cands = sky::DEFAULT_ENGINE_CANDS;
+  // the compiled launch shapes (warps per CTA, candidates per lane)
+  const uint32_t shapes[][2] = {{4, 4}, {8, 4}, {4, 2}, {8, 2}};
   const Knob knob_set[] = {
       {&sky_params::chunk_alpha_x4, {4, 8, 16, 32, 64}},
       {&sky_params::dom_block, {256, 512, 1024, 2048}},
@@ -93,6 +99,8 @@ sky_status tune(sky_ctx* ctx, const sky_query* queries, uint32_t nq, uint32_t ma
       ps[i].chunk_max = k.chunk_max;
       ps[i].chunk_alpha_x4 = k.chunk_alpha_x4;
       ps[i].dom_block = k.dom_block;
+      ps[i].engine_warps = k.engine_warps;
+      ps[i].engine_cands = k.engine_cands;
     }
     sky_status s = sky_skyline_batch(ctx, qs.data(), nq);
     if (s != SKY_OK) return s;
@@ -132,8 +140,28 @@ sky_status tune(sky_ctx* ctx, const sky_query* queries, uint32_t nq, uint32_t ma
         cur_ms = ms;
       }
     }
-  for (int sweep = 0; sweep < 2 && status == SKY_OK; ++sweep) {
+  // every launch shape at the knobs found so far
+  auto shape_pass = [&]() -> bool {
     bool changed = false;
+    for (const auto& sh : shapes) {
+      if (trials >= max_trials || status != SKY_OK) break;
+      if (cur.engine_warps == sh[0] && cur.engine_cands == sh[1]) continue;
+      sky_params cand = cur;
+      cand.engine_warps = sh[0];
+      cand.engine_cands = sh[1];
+      double ms = 0;
+      status = measure(cand, &ms);
+      if (status == SKY_OK && ms < cur_ms) {
+        cur = cand;
+        cur_ms = ms;
+        changed = true;
+      }
+    }
+    return changed;
+  };
+  shape_pass();
+  for (int sweep = 0; sweep < 2 && status == SKY_OK; ++sweep) {
+    bool changed = sweep > 0 && shape_pass();
     for (const Knob& k : knob_set) {
       for (uint32_t v : k.values) {
         if (trials >= max_trials || status != SKY_OK) break;
@@ -157,7 +185,8 @@ sky_status tune(sky_ctx* ctx, const sky_query* queries, uint32_t nq, uint32_t ma
   // three can favour a worse candidate.  Confirm the winner against the
   // starting knobs with the median of CONFIRM interleaved runs each.
   const bool moved = cur.chunk_min != start.chunk_min || cur.chunk_max != start.chunk_max ||
-                     cur.chunk_alpha_x4 != start.chunk_alpha_x4 || cur.dom_block != start.dom_block;
+                     cur.chunk_alpha_x4 != start.chunk_alpha_x4 || cur.dom_block != start.dom_block ||
+                     cur.engine_warps != start.engine_warps || cur.engine_cands != start.engine_cands;
   if (status == SKY_OK && moved) {
     constexpr int CONFIRM = 5;
     double a[CONFIRM], b[CONFIRM];
@@ -183,6 +212,8 @@ sky_status tune(sky_ctx* ctx, const sky_query* queries, uint32_t nq, uint32_t ma
   knobs->chunk_max = cur.chunk_max;
   knobs->chunk_alpha_x4 = cur.chunk_alpha_x4;
   knobs->dom_block = cur.dom_block;
+  knobs->engine_warps = cur.engine_warps;
+  knobs->engine_cands = cur.engine_cands;
   *best_ms = cur_ms;
   return SKY_OK;
 }

@@ -42,6 +42,8 @@ class SkyParams(ctypes.Structure):
         ("chunk_max", ctypes.c_uint32),
         ("chunk_alpha_x4", ctypes.c_uint32),
         ("dom_block", ctypes.c_uint32),
+        ("engine_warps", ctypes.c_uint32),
+        ("engine_cands", ctypes.c_uint32),
     ]
 
 
@@ -191,7 +193,8 @@ def load(build_if_missing: bool = True):
 
 def make_params(scheme="none", p: int = 1, slices=None, normalize=False, slice_dim=0, seed=0,
                 grid_filter=True, rep="none", reps_per_partition=1, merge="sequential",
-                exec="persistent", chunk_min=0, chunk_max=0, chunk_alpha_x4=0, dom_block=0) -> SkyParams:
+                exec="persistent", chunk_min=0, chunk_max=0, chunk_alpha_x4=0, dom_block=0,
+                engine_warps=0, engine_cands=0) -> SkyParams:
     L = load()
     sp = SkyParams()
     L.sky_params_init(ctypes.byref(sp))
@@ -210,6 +213,7 @@ def make_params(scheme="none", p: int = 1, slices=None, normalize=False, slice_d
     sp.exec = EXECS[exec] if isinstance(exec, str) else int(exec)
     sp.chunk_min, sp.chunk_max = int(chunk_min), int(chunk_max)
     sp.chunk_alpha_x4, sp.dom_block = int(chunk_alpha_x4), int(dom_block)
+    sp.engine_warps, sp.engine_cands = int(engine_warps), int(engine_cands)
     return sp
 
 
@@ -354,7 +358,7 @@ class Context:
 
     def autotune_batch(self, queries, max_trials: int = 0):
         """Tunes one set of engine knobs for a batch (sky_autotune_batch).
-        queries: list of (points, params).  Returns (dict of the four knobs,
+        queries: list of (points, params).  Returns (dict of the six knobs,
         best batch time in ms)."""
         nq = len(queries)
         arr = (SkyQuery * max(nq, 1))()
@@ -382,7 +386,8 @@ class Context:
         ms = ctypes.c_double(0)
         self._check(self._L.sky_autotune_batch(self._h, arr, nq, int(max_trials), ctypes.byref(knobs),
                                                ctypes.byref(ms)))
-        return ({k: getattr(knobs, k) for k in ("chunk_min", "chunk_max", "chunk_alpha_x4", "dom_block")},
+        return ({k: getattr(knobs, k) for k in ("chunk_min", "chunk_max", "chunk_alpha_x4", "dom_block",
+                                                 "engine_warps", "engine_cands")},
                 ms.value)
 
     def capture(self, queries):

@@ -99,8 +99,10 @@ def test_autotune_batch_keeps_results(ctx):
     xs = [datagen.anticorrelated(40000, 6, 61), datagen.anticorrelated(25000, 5, 62)]
     ps = [native.make_params(scheme="sliced", p=8), native.make_params(scheme="angular", slices=[2, 2, 2, 2])]
     want = [ctx.skyline(x, params=p) for x, p in zip(xs, ps)]
-    knobs, ms = ctx.autotune_batch(list(zip(xs, ps)), max_trials=10)
+    knobs, ms = ctx.autotune_batch(list(zip(xs, ps)), max_trials=16)
     assert ms > 0 and knobs["dom_block"] % 32 == 0 and knobs["chunk_max"] >= knobs["chunk_min"] > 0
+    # the launch shape (tile width, warps per CTA) is one of the compiled ones
+    assert knobs["engine_warps"] in (4, 8) and knobs["engine_cands"] in (2, 4)
     tuned = [native.make_params(scheme="sliced", p=8, **knobs),
              native.make_params(scheme="angular", slices=[2, 2, 2, 2], **knobs)]
     for g, w in zip(ctx.skyline_batch(list(zip(xs, tuned))), want):

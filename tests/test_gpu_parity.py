@@ -204,3 +204,29 @@ def test_invalid_inputs(ctx):
         ctx.skyline(datagen.independent(10, 3, 1), scheme="sliced", p=2, slice_dim=3)
     # the context stays usable after errors
     assert ctx.skyline(datagen.independent(100, 3, 1)).shape[0] > 0
+
+
+# Every compiled launch shape of the engine (warps per CTA x candidates per
+# lane: the tile width of a work item) gives the oracle's result, with the
+# default knobs and with small chunks and blocks that force many rounds.
+@pytest.mark.parametrize("warps,cands", [(4, 4), (8, 4), (4, 2), (8, 2)])
+def test_engine_launch_shapes(ctx, oracle_mod, warps, cands):
+    shape = dict(engine_warps=warps, engine_cands=cands)
+    x6 = datagen.anticorrelated(20011, 6, 81)
+    _check(ctx, oracle_mod, x6, "sliced", p=8, **shape)
+    _check(ctx, oracle_mod, x6, "angular", slices=[2, 2, 2, 1, 1], rep="sorted", merge="noseq", **shape)
+    _check(ctx, oracle_mod, x6, "random", p=5, seed=3, chunk_min=256, chunk_max=1024, dom_block=256, **shape)
+    x8 = datagen.independent(30001, 8, 82)
+    _check(ctx, oracle_mod, x8, "grid", slices=[2] * 8, **shape)
+    x3 = datagen.correlated(9001, 3, 83, quantised=False)
+    _check(ctx, oracle_mod, x3, "none", exec="plain", **shape)
+    _check(ctx, oracle_mod, x3[:1], "none", **shape)
+
+
+def test_engine_launch_shape_rejected(ctx):
+    from paper_2411_14968_gb300 import native
+    x = datagen.anticorrelated(1000, 4, 84)
+    for bad in (dict(engine_warps=2), dict(engine_cands=3), dict(engine_warps=16, engine_cands=4)):
+        with pytest.raises(native.SkylineError) as e:
+            ctx.skyline(x, **bad)
+        assert e.value.status == native.SKY_EINVAL
