@@ -52,6 +52,17 @@ def anticorrelated(n: int, d: int, seed: int) -> np.ndarray:
     return out
 
 
+def anticorrelated_blocks(n: int, d: int, seed: int, block: int = 10_000_000) -> np.ndarray:
+    """``anticorrelated`` drawn in independent blocks of ``block`` points
+    (block i from seed + i), so that very large inputs need memory for one
+    block's draws only; for n <= block it equals anticorrelated(n, d, seed)."""
+    out = np.empty((n, d), dtype=np.float32)
+    for i, lo in enumerate(range(0, n, block)):
+        hi = min(n, lo + block)
+        out[lo:hi] = anticorrelated(hi - lo, d, seed + i)
+    return out
+
+
 def independent(n: int, d: int, seed: int, quantised: bool = True) -> np.ndarray:
     rng = _rng(seed)
     x = rng.random(size=(n, d))
