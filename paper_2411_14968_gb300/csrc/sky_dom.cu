@@ -6,9 +6,11 @@
 // Both kernels are exact for the same reason as the engine: t is outside
 // Sky(r) iff some point of r dominates t, so testing a candidate against any
 // set of real input points never kills a skyline point.  A group is 32 * R
-// candidates in the registers of one warp (R per lane); the warp scans its
-// dominators with uniform loads, tests every candidate with FP32 compares
-// (Def. 1) and leaves as soon as a ballot shows every candidate dead.
+// candidates in the registers of one warp (R per lane); the warp leaves as
+// soon as a ballot shows every candidate dead.  The representative filter
+// scans its few dominators with uniform loads and FP32 compares (Def. 1);
+// NoSeq stages blocks of u in shared memory and rejects pairs on their FP16
+// images first.
 #include <algorithm>
 #include <cstdio>
 #include "sky_internal.cuh"
@@ -184,13 +186,156 @@ __device__ __forceinline__ bool in_pd(const NoSeqArgs& a, u32 i, u32 j) {
   return true;
 }
 
+// NoSeq's dominance test runs on the FP16 round-down images of u, as the
+// local-skyline engine's does.  Round-down is monotone, so an image of s
+// above t's means s is above t in that attribute and cannot dominate t; the
+// sign of an f16x2 difference t - s is the sign of the exact difference of
+// the images (a nonzero difference of two FP16 numbers never rounds to zero,
+// the images are finite), so the FP16 test only rejects pairs that fail
+// Def. 1, and every pair it passes is decided in FP32.  A candidate holds
+// its images duplicated per word, word k = (image k, image k); dominators
+// are staged as pairs, word k = (image k of the first, image k of the
+// second), so one subtraction per attribute tests two dominators.
+constexpr int NR = 4;                // NoSeq candidates per lane
+constexpr int NGS = 32 * NR;         // candidates per NoSeq group
+constexpr u32 INF2 = 0x7C007C00u;    // (+inf, +inf): a padding dominator fails every test
+constexpr u32 NEG_INF2 = 0xFC00FC00u;  // (-inf, -inf): a dead candidate passes no test
+
+__device__ __forceinline__ u32 hsub2_bits(u32 t, u32 w) {
+  u32 r;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(t), "r"(w));
+  return r;
+}
+// Bit 15 / 31 clear iff every attribute of the first / second dominator of
+// the pair is <= the candidate's (in FP16 images).
+template <int D>
+__device__ __forceinline__ u32 pair_fail(const u32 (&t)[D], const u32 (&w)[D]) {
+  u32 x = hsub2_bits(t[0], w[0]);
+#pragma unroll
+  for (int k = 1; k < D; ++k) x |= hsub2_bits(t[k], w[k]);
+  return x;
+}
+
+template <int D>
+struct NCand {
+  u32 t[NR][D];   // duplicated FP16 images (-inf when dead)
+  u32 pos[NR];    // position in u
+  bool alive[NR];
+  bool was[NR];
+};
+
+template <int D>
+__device__ __forceinline__ bool any_alive(const NCand<D>& c) {
+  bool a = false;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) a |= c.alive[r];
+  return a;
+}
+
+// Loads the group's candidates at u positions base + r * 32 + lane < end.
+template <int D>
+__device__ __forceinline__ void ns_load(const NoSeqArgs& a, u32 base, u32 end, int lane, NCand<D>& c) {
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    const u32 pos = base + r * 32 + lane;
+    const bool ok = pos < end && ld_cg_u8(a.ualive + pos);
+    const uint4 h = ok ? __ldg(a.uhc + pos) : make_uint4(0u, 0u, 0u, 0u);
+    const u32 w[4] = {h.x, h.y, h.z, h.w};
+    c.alive[r] = ok;
+    c.was[r] = ok;
+    c.pos[r] = pos;
+#pragma unroll
+    for (int k = 0; k < D; ++k) c.t[r][k] = ok ? __byte_perm(w[k / 2], 0u, (k & 1) ? 0x3232u : 0x1010u) : NEG_INF2;
+  }
+}
+
+// Def. 1 on the FP32 attributes: does u[j] dominate u[i]?
+template <int D>
+__device__ __forceinline__ bool dominates_u(const float4* __restrict__ upts, u32 j, u32 i) {
+  constexpr int V = vec_of(D);
+  float w[8], t[8];
+  load_point<D>(upts + (u64)j * V, false, w);
+  load_point<D>(upts + (u64)i * V, false, t);
+  bool le = true, ne = false;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    le &= w[k] <= t[k];
+    ne |= w[k] != t[k];
+  }
+  return le && ne;
+}
+
+// Tests the warp's candidates against u[lo..hi): 64 entries at a time are
+// staged as 32 dominator pairs in the warp's shared buffer sp (64 uint4; an
+// odd tail is padded with +inf images), then scanned with broadcast shared
+// loads.  Returns when every candidate is dead or the range is done.
+template <int D>
+__device__ void ns_scan_range(const NoSeqArgs& a, u32 lo, u32 hi, uint4* sp, NCand<D>& c) {
+  const int lane = threadIdx.x & 31;
+  for (u32 j0 = lo; j0 < hi; j0 += 64) {
+    {
+      const u32 e0 = j0 + 2 * lane, e1 = e0 + 1;
+      const uint4 z = make_uint4(INF2, INF2, INF2, INF2);
+      const uint4 p0 = e0 < hi ? __ldg(a.uhc + e0) : z;
+      const uint4 p1 = e1 < hi ? __ldg(a.uhc + e1) : z;
+      const u32 x0[4] = {p0.x, p0.y, p0.z, p0.w}, x1[4] = {p1.x, p1.y, p1.z, p1.w};
+      u32 w[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) w[k] = __byte_perm(x0[k / 2], x1[k / 2], (k & 1) ? 0x7632u : 0x5410u);
+      sp[2 * lane] = make_uint4(w[0], w[1], w[2], w[3]);
+      sp[2 * lane + 1] = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+    __syncwarp();
+    const u32 npairs = min(32u, (hi - j0 + 1) / 2);
+    for (u32 q = 0; q < npairs; ++q) {
+      u32 w[D];
+      const uint4 a0 = sp[2 * q];
+      w[0] = a0.x;
+      if (D > 1) w[1 < D ? 1 : 0] = a0.y;
+      if (D > 2) w[2 < D ? 2 : 0] = a0.z;
+      if (D > 3) w[3 < D ? 3 : 0] = a0.w;
+      if (D > 4) {
+        const uint4 a1 = sp[2 * q + 1];
+        w[4 < D ? 4 : 0] = a1.x;
+        if (D > 5) w[5 < D ? 5 : 0] = a1.y;
+        if (D > 6) w[6 < D ? 6 : 0] = a1.z;
+        if (D > 7) w[7 < D ? 7 : 0] = a1.w;
+      }
+      u32 acc = 0xffffffffu;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) acc &= pair_fail<D>(c.t[r], w);
+      if ((acc & 0x80008000u) != 0x80008000u) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const u32 x = pair_fail<D>(c.t[r], w);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const u32 jd = j0 + 2 * q + h;
+            if (c.alive[r] && !((x >> (15 + 16 * h)) & 1u) && jd < hi && dominates_u<D>(a.upts, jd, c.pos[r])) {
+              c.alive[r] = false;
+#pragma unroll
+              for (int k = 0; k < D; ++k) c.t[r][k] = NEG_INF2;
+            }
+          }
+        }
+      }
+      if ((q & 7) == 7 && !__any_sync(FULL, any_alive(c))) {
+        __syncwarp();
+        return;
+      }
+    }
+    __syncwarp();  // the buffer is restaged only after every lane's reads
+    if (!__any_sync(FULL, any_alive(c))) return;
+  }
+}
+
 // Items: (group of u_i, dominator block of u).  gpre[P + 1]: prefix of the
 // group counts per partition (computed on the device).
 template <int D>
 __global__ void __launch_bounds__(THREADS) k_noseq(NoSeqArgs a, const u32* __restrict__ gpre, const u32* nu_dev,
                                                    u32* counter) {
-  constexpr int V = vec_of(D);
-  const int lane = threadIdx.x & 31;
+  __shared__ uint4 s_pairs[WARPS][64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 nu = *nu_dev;
   const u32 ngroups = gpre[a.P];
   const u32 DB = a.dom_block;
@@ -213,13 +358,12 @@ __global__ void __launch_bounds__(THREADS) k_noseq(NoSeqArgs a, const u32* __res
       }
       const u32 i = lo;
       const u32 ibeg = __ldg(a.useg + i), iend = __ldg(a.useg + i + 1);
-      const u32 base = ibeg + (G - __ldg(gpre + i)) * GS;
-      const u32 gend = min(base + GS, iend);
+      const u32 base = ibeg + (G - __ldg(gpre + i)) * NGS;
+      const u32 gend = min(base + NGS, iend);
       const float fmax = __ldg(a.uscore + gend - 1);
       // dominator block [blo, bhi) of u; visit the partitions it overlaps
       const u32 blo = b * DB, bhi = min(blo + DB, nu);
-      Cand<D> c;
-      bool was[R];
+      NCand<D> c;
       bool loaded = false;
       u32 pos = blo;
       while (pos < bhi) {
@@ -246,26 +390,27 @@ __global__ void __launch_bounds__(THREADS) k_noseq(NoSeqArgs a, const u32* __res
           }
           if (cut > pos) {
             if (!loaded) {
-              load_cands<D>(a.upts, a.ualive, base, gend, lane, c, was);
+              ns_load<D>(a, base, gend, lane, c);
               loaded = true;
             }
-            bool any = false;
-#pragma unroll
-            for (int r = 0; r < R; ++r) any |= c.alive[r];
-            if (!__any_sync(FULL, any)) break;
-            scan_block<D>(a.upts + (u64)pos * V, cut - pos, false, c);
+            if (!__any_sync(FULL, any_alive(c))) break;
+            ns_scan_range<D>(a, pos, cut, s_pairs[warp], c);
           }
         }
         pos = jend;
       }
-      if (loaded) store_kills<D>(a.ualive, base, lane, c, was);
+      if (loaded) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+          if (c.was[r] && !c.alive[r]) a.ualive[c.pos[r]] = 0;
+      }
     }
   }
 }
 
 __global__ void k_noseq_groups(const u32* __restrict__ useg, u32 P, u32* __restrict__ cnt) {
   u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < P) cnt[i] = (useg[i + 1] - useg[i] + GS - 1) / GS;
+  if (i < P) cnt[i] = (useg[i + 1] - useg[i] + NGS - 1) / NGS;
 }
 
 // Segment descriptors of the local phase from the partition offsets;

@@ -307,6 +307,7 @@ cudaError_t launch_relative(const float* cand, u8* alive, u64 nc, const float* d
 // t in u_i is killed iff some s in pd_i dominates it.
 struct NoSeqArgs {
   const float4* upts;
+  const uint4* uhc;  // FP16 round-down images of u (packed, two per word)
   const float* uscore;
   const u32* useg;   // P + 1
   u8* ualive;

@@ -828,6 +828,7 @@ sky_status Runner::enqueue(BatchState& B) {
       CK(cudaMemsetAsync(b.ualive, 1, n, st));
       NoSeqArgs na{};
       na.upts = reinterpret_cast<const float4*>(b.upts);
+      na.uhc = b.uhc;
       na.uscore = b.uscore;
       na.useg = b.useg;
       na.ualive = b.ualive;
