@@ -104,7 +104,7 @@ class ClockSampler:
 
 
 ENGINE_PROFILE = os.path.join(ROOT, "profiles", "k_engine_bench_ant1m_d6.txt")
-ENGINE_SOURCE = os.path.join(ROOT, "paper_2411_14968_gb300", "csrc", "sky_engine.cu")
+ENGINE_SOURCE = os.path.join(ROOT, "paper_2411_14968_gb300", "csrc", "sky_engine_impl.cuh")
 
 
 def engine_traffic():
@@ -615,8 +615,10 @@ def sweeps_experiment(local: int):
     """Section 5 (operating-parameter sweeps on anticorrelated data, defaults
     N = 1M, d = 4, p = 120): GPU time of the global skyline and the size of
     the local-skyline union for the plain strategies and the improved ones,
-    varying N, d and p one at a time.  Grid and Angular reach p = 120 with
-    per-dimension / per-angle slice counts (2,3,4,5) and (6,5,4)."""
+    varying N (1e5 to 1e8, the paper's range), d (2 to 7) and p (60 to
+    3600) one at a time.  Grid and Angular reach p = 120 with per-dimension
+    / per-angle slice counts (2,3,4,5) and (6,5,4).  Every result is
+    compared with the oracle's skyline of the same input."""
     import torch
     from paper_2411_14968_gb300 import datagen, native
 
@@ -637,14 +639,24 @@ def sweeps_experiment(local: int):
             "noseq": dict(scheme="sliced", p=p, rep="sorted", merge="noseq"),
         }
 
+    import hashlib
+    gold_path = os.path.join(ROOT, "tests", "golden", "sweep_skylines.json")
+    gold = json.load(open(gold_path)) if os.path.exists(gold_path) else {}
     rows = []
     with native.Context(local) as ctx:
         ctx.set_timing(True)
 
-        def run(x, d, p, names, tag):
+        def run(n, d, seed, p, names, tag):
+            # every result is checked against the oracle's skyline of the same
+            # input (|Sky| and SHA-256 of the ascending indices, written by
+            # tests/golden/make_sweeps.py)
+            x = datagen.anticorrelated_blocks(n, d, seed)
+            g = gold.get(f"n={n},d={d},seed={seed}")
+            if g:
+                assert hashlib.sha256(x.astype("<f4").tobytes()).hexdigest() == g["input_sha256"], (n, d, seed)
             xt = torch.from_numpy(x).cuda()
+            del x
             strat = strategies(d, p)
-            sky = None
             for name in names:
                 pr = native.make_params(**strat[name])
                 ctx.skyline(xt, params=pr)  # warm-up (workspace)
@@ -653,20 +665,27 @@ def sweeps_experiment(local: int):
                     r = ctx.skyline(xt, params=pr)
                     ms.append(ctx.stats()["ms_total"])
                 st = ctx.stats()
-                sky = int(r.shape[0]) if sky is None else sky
-                assert sky == int(r.shape[0])
-                rows.append({"sweep": tag, "n": x.shape[0], "d": d, "p": st["partitions"], "strategy": name,
-                             "ms": round(min(ms), 3), "local_union": st["local_union"], "skyline": sky})
+                idx = r.cpu().numpy().astype("<u4")
+                match = None
+                if g:
+                    match = (idx.shape[0] == g["skyline"] and
+                             hashlib.sha256(idx.tobytes()).hexdigest() == g["skyline_sha256"])
+                    assert match, (tag, n, d, p, name)
+                rows.append({"sweep": tag, "n": n, "d": d, "p": st["partitions"], "strategy": name,
+                             "ms": round(min(ms), 3), "local_union": st["local_union"], "skyline": int(idx.shape[0]),
+                             "points_per_s": n / (min(ms) * 1e-3), "oracle_match": match})
                 print(json.dumps(rows[-1]), flush=True)
+            del xt
+            torch.cuda.empty_cache()
 
         plain = ["random", "grid", "angular", "sliced"]
         improved = ["sliced+", "angular+", "noseq"]
-        for n in (100_000, 500_000, 1_000_000, 5_000_000, 10_000_000):
-            run(datagen.anticorrelated(n, 4, 7), 4, 120, plain + improved, "size")
+        for n in (100_000, 500_000, 1_000_000, 5_000_000, 10_000_000, 50_000_000, 100_000_000):
+            run(n, 4, 7, 120, plain + improved, "size")
         for d in (2, 3, 5, 6, 7):
-            run(datagen.anticorrelated(1_000_000, d, 8), d, 120, improved, "dimensions")
+            run(1_000_000, d, 8, 120, improved, "dimensions")
         for p in (60, 240, 480, 720, 1200, 2400, 3600):
-            run(datagen.anticorrelated(1_000_000, 4, 7), 4, p, ["sliced+", "noseq"], "partitions")
+            run(1_000_000, 4, 7, p, ["sliced+", "noseq"], "partitions")
     print(json.dumps({"experiment": "sweeps (anticorrelated; defaults N=1e6, d=4, p=120)", "rows": rows}), flush=True)
 
 
@@ -755,6 +774,18 @@ def ncu_case(which: str):
     (local phase, merge) of the second call are the captured ones."""
     import torch
     from paper_2411_14968_gb300 import datagen, native
+    if which == "c3":
+        # one 4M-point d = 8 quantised independent query, Grid m = 2 (256
+        # cells): the workload where the memory-bound stages bound the query
+        x = datagen.independent(4_000_000, 8, 3)
+        xt = torch.from_numpy(x).cuda()
+        with native.Context(0) as ctx:
+            p = native.make_params(scheme="grid", slices=[2] * 8)
+            for _ in range(2):
+                r = ctx.skyline(xt, params=p)
+            torch.cuda.synchronize()
+            print(f"ncu case c3: |Sky| = {r.shape[0]}, {ctx.stats()['launches']} launches per call")
+        return
     n = 200_000 if which == "small" else N
     x = datagen.anticorrelated(n, D, SEED)
     xt = torch.from_numpy(x).cuda()
@@ -783,9 +814,10 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--experiment", choices=["rep-filtering", "sweeps", "configs", "shapes"], default=None,
                     help="run one of the paper's experiments instead of the benchmark")
-    ap.add_argument("--ncu-case", choices=["small", "batch"], default=None,
+    ap.add_argument("--ncu-case", choices=["small", "batch", "c3"], default=None,
                     help="run a profiling case only, twice, default knobs, no timing: 'small' = one query "
-                         "(anticorrelated N=200k, d=6, Sliced p=64); 'batch' = the benchmark's batched step")
+                         "(anticorrelated N=200k, d=6, Sliced p=64); 'batch' = the benchmark's batched step; "
+                         "'c3' = one quantised independent query, N=4M, d=8, Grid m=2")
     # FP32 compare peak in T compares/s; 0 derives it from the device's SM
     # count x 64 compare lanes per SM per clock x the maximum SM clock seen
     ap.add_argument("--compare-peak-tcmp", type=float, default=0.0)
