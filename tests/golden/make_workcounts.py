@@ -1,12 +1,18 @@
-"""Writes workcounts_ant_1m_d6.json: the oracle's dominance-test counts on the
-1,000,000-point anticorrelated d = 6 workload (seed 1) for each variant the
-benchmark times.
+"""Writes workcounts_<workload>.json: the oracle's dominance-test counts for
+each variant the benchmark times -- on the 1,000,000-point anticorrelated
+d = 6 workload (seed 1: workcounts_ant_1m_d6.json) and on the 2,000,000-point
+skewed d = 6 workload (seed 4, Angular (4,4,2,2,2) on x / column max with
+Sorted representatives, sequential final phase:
+workcounts_skewed_2m_d6.json).
 
 The count of one variant is the number of pairwise dominance tests the
 plain CPU oracle makes (SFS window tests of Algorithm 1 in every partition,
 plus the tests of the final phase), i.e. the algorithmic work of the
 dominance kernels; one test is d attribute compares.  Calls only oracle/ and
-the seeded generator.  Run: python tests/golden/make_workcounts.py
+the seeded generator.  The local skylines of Algorithm 2 run over every host
+core (the counts do not depend on the thread count; the sequential final
+phase stays single-threaded).  Run: python tests/golden/make_workcounts.py
+[workload ...]
 """
 from __future__ import annotations
 
@@ -23,19 +29,31 @@ sys.path.insert(0, ROOT)
 from oracle import oracle as O  # noqa: E402
 from paper_2411_14968_gb300 import datagen  # noqa: E402
 
-N, D, SEED = 1_000_000, 6, 1
-VARIANTS = {
-    "sliced": dict(scheme=O.SLICED, p=64),
-    "sliced_rep": dict(scheme=O.SLICED, p=64, rep=O.REP_SORTED),
-    "angular": dict(scheme=O.ANGULAR, slices=[4, 2, 2, 2, 2]),
-    "angular_rep": dict(scheme=O.ANGULAR, slices=[4, 2, 2, 2, 2], rep=O.REP_SORTED),
+# workload -> (generator kind, N, d, seed, variants)
+WORKLOADS = {
+    "ant_1m_d6": ("anticorrelated", 1_000_000, 6, 1, {
+        "sliced": dict(scheme=O.SLICED, p=64),
+        "sliced_rep": dict(scheme=O.SLICED, p=64, rep=O.REP_SORTED),
+        "angular": dict(scheme=O.ANGULAR, slices=[4, 2, 2, 2, 2]),
+        "angular_rep": dict(scheme=O.ANGULAR, slices=[4, 2, 2, 2, 2], rep=O.REP_SORTED),
+    }),
+    "skewed_2m_d6": ("skewed", 2_000_000, 6, 4, {
+        "angular_rep": dict(scheme=O.ANGULAR, slices=[4, 4, 2, 2, 2], normalize=True, rep=O.REP_SORTED),
+    }),
 }
 
 
-def main():
-    x = datagen.anticorrelated(N, D, SEED)
-    out = {"workload": f"anticorrelated N={N} d={D} seed={SEED}", "machine": platform.machine(), "variants": {}}
-    for name, kw in VARIANTS.items():
+def main(names):
+    for wl in names or WORKLOADS:
+        run(wl)
+
+
+def run(wl):
+    kind, N, D, SEED, variants = WORKLOADS[wl]
+    x = datagen.make(kind, N, D, SEED)
+    O.set_threads(os.cpu_count() or 1)
+    out = {"workload": f"{kind} N={N} d={D} seed={SEED}", "machine": platform.machine(), "variants": {}}
+    for name, kw in variants.items():
         t = time.time()
         r = O.partitioned(x, **kw)
         st = r["stage"]
@@ -47,9 +65,10 @@ def main():
             "oracle_seconds": round(time.time() - t, 1),
         }
         print(name, out["variants"][name], flush=True)
-    with open(os.path.join(HERE, "workcounts_ant_1m_d6.json"), "w") as fh:
+    O.set_threads(1)
+    with open(os.path.join(HERE, f"workcounts_{wl}.json"), "w") as fh:
         json.dump(out, fh, indent=1)
 
 
 if __name__ == "__main__":
-    main()
+    main(sys.argv[1:])
