@@ -710,6 +710,9 @@ def configs_experiment(local: int):
           dict(scheme="angular", slices=[4, 4, 2, 2, 2], normalize=True, rep="sorted", merge="noseq")]),
     ]
     out = []
+    wc_path = os.path.join(ROOT, "tests", "golden", "workcounts_skewed_2m_d6.json")
+    skewed_wc = json.load(open(wc_path))["variants"]["angular_rep"] if os.path.exists(wc_path) else None
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     with native.Context(local) as ctx:
         ctx.set_timing(True)
         for title, (kind, n, d, seed), variants in cases:
@@ -723,9 +726,18 @@ def configs_experiment(local: int):
                     r = ctx.skyline(xt, params=p)
                     ms.append(ctx.stats()["ms_total"])
                 st = ctx.stats()
-                row["variants"].append({"params": kw, "ms": round(min(ms), 3),
-                                        "points_per_s": n / (min(ms) * 1e-3), "skyline": int(r.shape[0]),
-                                        "local_union": st["local_union"]})
+                v = {"params": kw, "ms": round(min(ms), 3), "points_per_s": n / (min(ms) * 1e-3),
+                     "skyline": int(r.shape[0]), "local_union": st["local_union"],
+                     "ms_dom_local": round(st["ms_dom_local"], 3), "ms_dom_merge": round(st["ms_dom_merge"], 3)}
+                if kind == "skewed" and kw.get("merge", "sequential") == "sequential" and skewed_wc:
+                    # compare-pipe roofline of the engine on this workload: the
+                    # oracle's SFS test count x d over the two engine launches
+                    t = skewed_wc["local_tests"] + skewed_wc["merge_tests"]
+                    dom = st["ms_dom_local"] + st["ms_dom_merge"]
+                    peak = sms * 64 * 2.07e9
+                    v["roofline"] = {"algorithmic_tests": t, "achieved_tcmp": t * d / (dom * 1e-3) / 1e12,
+                                     "frac_of_derived_fp32_peak": t * d / (dom * 1e-3) / peak}
+                row["variants"].append(v)
             if len(variants) > 1:
                 ps = [native.make_params(**kw) for kw in variants]
                 ctx.skyline_batch([(xt, p) for p in ps])
