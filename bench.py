@@ -781,6 +781,54 @@ def shapes_experiment(local: int):
     print(json.dumps({"experiment": "engine launch shapes on the batched step", "rows": rows}), flush=True)
 
 
+def fp16_images(x):
+    """Round-down FP16 images of FP32 values, clamped to the finite FP16
+    range (the images the dominance kernels test first)."""
+    h = x.astype(np.float16)
+    down = h.astype(np.float32) > x
+    h[down] = np.nextafter(h[down], np.float16(-np.inf))
+    return np.clip(h, np.float16(-65504.0), np.float16(65504.0))
+
+
+def fp16_experiment():
+    """How often the FP16 test passes a pair that Def. 1 then rejects, on
+    each workload's data (host-side, numpy): 3000 x 3000 sampled pairs (s, t)
+    with score(s) <= score(t); pass = every image of s <= t's, dominates =
+    Def. 1 on the FP32 values.  pass & not dominates is the FP32 work the
+    images cannot save (ties of images, or of the values themselves)."""
+    from paper_2411_14968_gb300 import datagen
+    rng = np.random.default_rng(3)
+    cases = [("anticorrelated N=1e6 d=6", datagen.anticorrelated(1_000_000, 6, 1)),
+             ("independent quantised N=4e6 d=8", datagen.independent(4_000_000, 8, 3)),
+             ("skewed N=2e6 d=6", datagen.skewed(2_000_000, 6, 4))]
+    out = []
+    for name, x in cases:
+        idx = rng.choice(x.shape[0], 3000, replace=False)
+        jdx = rng.choice(x.shape[0], 3000, replace=False)
+        t, sp = x[idx], x[jdx]
+        ht, hs = fp16_images(t), fp16_images(sp)
+        ft = t.astype(np.float32).sum(axis=1, dtype=np.float32)
+        fs = sp.astype(np.float32).sum(axis=1, dtype=np.float32)
+        order = fs[:, None] <= ft[None, :]
+        pas = np.ones((3000, 3000), bool)
+        le = np.ones((3000, 3000), bool)
+        ne = np.zeros((3000, 3000), bool)
+        for k in range(x.shape[1]):
+            pas &= hs[:, k][:, None] <= ht[:, k][None, :]
+            le &= sp[:, k][:, None] <= t[:, k][None, :]
+            ne |= sp[:, k][:, None] != t[:, k][None, :]
+        dom = le & ne & order
+        pas &= order
+        npairs = int(order.sum())
+        row = {"workload": name, "pairs": npairs, "fp16_pass": float(pas.sum() / npairs),
+               "dominates": float(dom.sum() / npairs),
+               "pass_not_dominates": float((pas & ~dom).sum() / npairs),
+               "fp32_checks_per_kill": float(pas.sum() / max(1, dom.sum()))}
+        out.append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps({"experiment": "FP16 image test vs Def. 1 on sampled pairs", "rows": out}), flush=True)
+
+
 def ncu_case(which: str):
     """The cases the engine's ncu captures run: the two k_engine launches
     (local phase, merge) of the second call are the captured ones."""
@@ -824,7 +872,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--experiment", choices=["rep-filtering", "sweeps", "configs", "shapes"], default=None,
+    ap.add_argument("--experiment", choices=["rep-filtering", "sweeps", "configs", "shapes", "fp16"], default=None,
                     help="run one of the paper's experiments instead of the benchmark")
     ap.add_argument("--ncu-case", choices=["small", "batch", "c3"], default=None,
                     help="run a profiling case only, twice, default knobs, no timing: 'small' = one query "
@@ -850,6 +898,9 @@ def main():
         return
     if args.experiment == "shapes":
         shapes_experiment(local)
+        return
+    if args.experiment == "fp16":
+        fp16_experiment()
         return
     if args.impl == "reference":
         reference_arm(args, rank, world)
