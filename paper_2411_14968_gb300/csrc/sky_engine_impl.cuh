@@ -669,6 +669,7 @@ struct Meta {
   u32 dense;   // 1: the dominators are dense-list points (FP32 via dpos)
   u32 copied;  // 1: a bulk copy into the item's buffer was issued
   u32 counted; // 1: the producer counted the item towards its tile (empty item completing the tile)
+  u32 parity;  // phase parity of the buffer's barrier that the copy completes
 };
 
 struct Shared {
@@ -676,7 +677,6 @@ struct Shared {
   u32 spos[WARPS][GS];
   Meta meta[2];
   u64 bar[2];
-  u32 bar_phase[2];
   u32 cursor;
   u32 flag;
   u32 wtot[WARPS];
@@ -685,6 +685,7 @@ struct Shared {
   int pslot;    // buffer slot of the next item
   uint4* pbuf;  // and its buffer
   u32 abort_seen;  // the launch's abort flag was seen set
+  u32 pcopies[2];  // bulk copies issued into each buffer (by its producers, one at a time)
 };
 
 // Tile status words of the ordered compaction (decoupled look-back): the
@@ -775,6 +776,8 @@ __device__ void produce(const Params& P, Shared& S, int slot, uint4* buf) {
   if (m.cnt) {
     // whole pairs: m.base is even, the block is m.cnt entries rounded up
     const u32 bytes = ((m.cnt + 1) & ~1u) * 16u;
+    m.parity = S.pcopies[slot] & 1u;
+    ++S.pcopies[slot];
     fence_proxy_async();
     mbar_expect_tx(&S.bar[slot], bytes);
     bulk_g2s(buf, codes, bytes, &S.bar[slot]);
@@ -809,6 +812,24 @@ __device__ void load_cand(const SegDesc& sd, u32 pos, bool valid, CandsT<D, R>& 
     unpack_dup<D>(h, c.t[r]);
   } else {
     set_dead<D>(c.t[r]);
+  }
+}
+
+// After the last tile of a phase A (one thread): publish phase B over the
+// dense list of dl points, or the next round if nothing survived.
+__device__ void after_phase_a(const Params& P, const SegDesc& sd, u32 s, const SegState& cs, u32 dl) {
+  if (dl == 0) {
+    SegState nx;
+    nx.cur = cs.cend;
+    nx.wlen = cs.wlen;
+    nx.rounds = cs.rounds + 1;
+    start_round(P, sd, s, nx);
+  } else {
+    const u32 DB = P.cfg.dom_block;
+    const u32 wb = ceil_div(cs.wlen, DB);
+    const u32 wbB = wb > A_BLOCKS ? wb - A_BLOCKS : 0;
+    const u32 dtiles = ceil_div(dl, TILE);
+    publish(P, s, 1, dtiles, dtiles * (wbB + ceil_div(dl, DB)));
   }
 }
 
@@ -959,6 +980,18 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
   __threadfence();
   fence_proxy_async();
   __syncthreads();
+  if (!P.cfg.ordered) {
+    // one thread counts the tile and, for the phase's last tile, publishes
+    // phase B: the other threads have nothing left to do in this item
+    if (threadIdx.x == 0) {
+      const u32 old = atomicAdd(&st->done_a, 1u);
+      if (old == cs.tiles - 1) {
+        __threadfence();
+        after_phase_a(P, sd, s, cs, atomicAdd(&st->dlen, 0u));
+      }
+    }
+    return;
+  }
   if (threadIdx.x == 0) {
     const u32 old = atomicAdd(&st->done_a, 1u);
     S.flag = old == cs.tiles - 1;
@@ -970,7 +1003,7 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
   __syncthreads();
   if (!S.flag) return;
   const u32 dl = S.tile_base;
-  if (P.cfg.ordered) {
+  {
     // last tile of phase A: every tile has finished its look-back, so its
     // status word is free.  It now holds the dense tile's end for phase B:
     // the tile's last position, or the whole list when a run of equal
@@ -989,23 +1022,7 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
     __threadfence();
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    {
-      // publish phase B, or the next round if nothing survived
-      if (dl == 0) {
-        SegState nx;
-        nx.cur = cs.cend;
-        nx.wlen = cs.wlen;
-        nx.rounds = cs.rounds + 1;
-        start_round(P, sd, s, nx);
-      } else {
-        const u32 wb = ceil_div(cs.wlen, DB);
-        const u32 wbB = wb > A_BLOCKS ? wb - A_BLOCKS : 0;
-        const u32 dtiles = ceil_div(dl, TILE);
-        publish(P, s, 1, dtiles, dtiles * (wbB + ceil_div(dl, DB)));
-      }
-    }
-  }
+  if (threadIdx.x == 0) after_phase_a(P, sd, s, cs, dl);
 }
 
 // Phase B item: dense tile against window block A_BLOCKS + b, or dense block
@@ -1181,11 +1198,11 @@ __global__ void __launch_bounds__(THREADS, 16 / WARPS) k_engine(Params P) {
   if (threadIdx.x == 0) {
     mbar_init(&S.bar[0]);
     mbar_init(&S.bar[1]);
-    S.bar_phase[0] = S.bar_phase[1] = 0;
     S.cursor = 0;
     S.meta[0].state = M_EMPTY;
     S.meta[1].state = M_EMPTY;
     S.abort_seen = 0;
+    S.pcopies[0] = S.pcopies[1] = 0;
   }
   __syncthreads();
   if (blockIdx.x == 0 && !prologue(P)) return;
@@ -1196,7 +1213,10 @@ __global__ void __launch_bounds__(THREADS, 16 / WARPS) k_engine(Params P) {
     uint4* const cur_buf = buf0 + (size_t)slot * BUFN;
     // wait until the slot's ticket has a task (or there is no more work)
     if (threadIdx.x == 0) {
-      // every warp has left the previous item (and its producer call)
+      // every warp is past the previous item's last CTA barrier, so every
+      // thread has copied that item's plan and left its producer call: its
+      // buffer slot is free for the next plan
+      if (k > 0) S.meta[slot ^ 1].state = M_EMPTY;
       S.pclaim = 0;
       S.pslot = slot ^ 1;
       S.pbuf = buf0 + (size_t)(slot ^ 1) * BUFN;
@@ -1224,11 +1244,8 @@ __global__ void __launch_bounds__(THREADS, 16 / WARPS) k_engine(Params P) {
     __syncthreads();
     const Meta m = S.meta[slot];
     if (m.state != M_READY) break;
-    if (m.copied && !mbar_wait(&S.bar[slot], S.bar_phase[slot], P.wait_ns, P.err, P.ctl)) break;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      if (m.copied) S.bar_phase[slot] ^= 1u;
-      S.meta[slot].state = M_EMPTY;
+    if (m.copied) {
+      if (!mbar_wait(&S.bar[slot], m.parity, P.wait_ns, P.err, P.ctl)) break;
     }
     const SegDesc sd = P.segs[m.s];
     switch (sd.d) {
@@ -1242,13 +1259,15 @@ __global__ void __launch_bounds__(THREADS, 16 / WARPS) k_engine(Params P) {
       default: run_item<8>(P, sd, m, cur_buf, S); break;
     }
     if (threadIdx.x == 0) atomicAdd(P.ctl + C_PROGRESS, 1u);
-    __syncthreads();
-    // an abort raised while this item ran is seen after the next one
+    // No CTA barrier here: past the item's last barrier the threads read
+    // only abort_seen (set before it, in produce_next) and, on an abort, the
+    // prefetched plan; thread 0 rewrites neither before the next item's
+    // first barrier.  An abort raised while this item ran is seen after the
+    // next one.
     if (S.abort_seen) {
       // the copy of the prefetched item may still be in flight
       const Meta mn = S.meta[slot ^ 1];
-      if (mn.state == M_READY && mn.copied)
-        mbar_wait(&S.bar[slot ^ 1], S.bar_phase[slot ^ 1], P.wait_ns, P.err, P.ctl);
+      if (mn.state == M_READY && mn.copied) mbar_wait(&S.bar[slot ^ 1], mn.parity, P.wait_ns, P.err, P.ctl);
       break;
     }
   }
