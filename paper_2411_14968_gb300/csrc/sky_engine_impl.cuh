@@ -24,14 +24,17 @@
 //      dominator killed in phase A was itself dominated by a window point
 //      that also dominates the candidate, so the dense list holds every chunk
 //      dominator that matters); the survivors are appended to the window.
-// In an ordered launch (the merge) the dense list is kept in position (=
-// score) order -- each tile writes its survivors at the sum of its
-// predecessors' counts, found by decoupled look-back -- so phase B tests a
+// When the dense list is kept in position (= score) order, phase B tests a
 // dense tile only against the dense entries up to its end (extended over a
-// run of equal scores), half of the square.  The look-back makes a tile wait
-// for the scans of the tiles before it, which pays off for the merge's large
-// chunks but not for the local phase's many small segments, so local-phase
-// launches compact in arrival order and test the whole dense list.
+// run of equal scores), half of the square.  The merge (and a local phase
+// of few segments) keeps the order by decoupled look-back: each tile writes
+// its survivors at the sum of its predecessors' counts.  The look-back makes
+// a tile wait for the scans of the tiles before it, which pays off for large
+// chunks but blocks CTAs when many small segments interleave, so a local
+// phase of many segments keeps the order differently: its phase-A tiles
+// only count, and the phase's last tile compacts the whole chunk in order.
+// One CTA does that pass, so a round whose chunk is long falls back to
+// arrival order and tests the whole dense square.
 //
 // Work queue.  Segments advance through their rounds independently; there
 // is no grid-wide barrier.  A phase of a segment is a task of items (tile of
@@ -566,6 +569,13 @@ __device__ void plan_round(const SegDesc& sd, const EngineCfg& cfg, SegState& s)
   s.tiles = ceil_div(s.cend - s.cur, TILE);
 }
 
+// How the round whose chunk is [cur, cend) builds its dense list: the
+// launch's mode, except that ORD_LAST falls back to arrival order for a
+// chunk longer than ORD_LAST_MAX (one CTA would compact it alone).
+__device__ __forceinline__ u32 round_ord(const EngineCfg& cfg, u32 cur, u32 cend) {
+  return cfg.ordered == ORD_LAST && cend - cur > ORD_LAST_MAX ? ORD_NONE : cfg.ordered;
+}
+
 // Publishes a task (one thread).  The 64-bit atomic reserves the task index
 // and its ticket range together.
 __device__ void publish(const Params& P, u32 s, u32 phase, u32 tiles, u32 items) {
@@ -754,7 +764,8 @@ __device__ void produce(const Params& P, Shared& S, int slot, uint4* buf) {
       // tile t can only be dominated by dense entries up to the end of the
       // tile, extended over a run of scores equal to its last one (the end
       // the last phase-A tile wrote into the tile's status word)
-      const u32 e = P.cfg.ordered ? ld_cg_u32(P.tstat + m.tgid) : dlen;
+      const u32 ord = round_ord(P.cfg, ld_cg_u32(&P.st[m.s].cur), ld_cg_u32(&P.st[m.s].cend));
+      const u32 e = ord != ORD_NONE ? ld_cg_u32(P.tstat + m.tgid) : dlen;
       m.base = (b - wbB) * DB;
       m.cnt = m.base < e ? min(DB, e - m.base) : 0;
       m.dense = 1;
@@ -833,6 +844,58 @@ __device__ void after_phase_a(const Params& P, const SegDesc& sd, u32 s, const S
   }
 }
 
+// The survivors of the chunk [cur, cend) of a segment, compacted by the whole
+// CTA into the dense list in position order (ORD_LAST, by the phase's last
+// tile once every tile's flags are final); sets the list's length and
+// returns it.  Thread t takes PER consecutive positions of each step, so a
+// block-wide exclusive scan of the threads' counts gives every survivor its
+// slot.
+template <int D>
+__device__ u32 compact_chunk(const SegDesc& sd, SegState* st, u32 cur, u32 cend, Shared& S) {
+  constexpr u32 PER = 8;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  u32 base = 0;
+  for (u32 p0 = cur; p0 < cend; p0 += THREADS * PER) {
+    const u32 q0 = p0 + threadIdx.x * PER;
+    u32 fl = 0;
+#pragma unroll
+    for (u32 i = 0; i < PER; ++i)
+      if (q0 + i < cend && ld_cg_u8(sd.alive + q0 + i)) fl |= 1u << i;
+    const u32 c = __popc(fl);
+    u32 x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 y = __shfl_up_sync(FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) S.wtot[warp] = x;
+    __syncthreads();
+    u32 off = base + x - c;
+    u32 tot = 0;
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) {
+      const u32 v = S.wtot[w];
+      if (w < warp) off += v;
+      tot += v;
+    }
+    while (fl) {
+      const u32 i = __ffs(fl) - 1;
+      fl &= fl - 1;
+      const u32 pos = q0 + i;
+      sd.dpos[off] = pos;
+      put_pair_entry<D>(sd.dhc, off, __ldg(sd.hc + pos));
+      ++off;
+    }
+    base += tot;
+    __syncthreads();  // S.wtot is rewritten by the next step
+  }
+  if (threadIdx.x == 0) st->dlen = base;
+  __threadfence();
+  fence_proxy_async();
+  __syncthreads();
+  return base;
+}
+
 // Phase A item: tile `tile` of the chunk against window block 0.
 template <int D>
 __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const uint4* staged, Shared& S) {
@@ -843,11 +906,7 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
   SegState cs;
   cs.cur = ld_cg_u32(&st->cur);
   cs.cend = ld_cg_u32(&st->cend);
-  cs.wlen = ld_cg_u32(&st->wlen);
-  cs.tiles = ld_cg_u32(&st->tiles);
-  cs.rounds = ld_cg_u32(&st->rounds);
   const u32 cnt = mt.cnt;
-  const u32 per_tile = max(1u, min(ceil_div(cs.wlen, DB), A_BLOCKS));
   const u32 gbase = cs.cur + mt.tile * TILE + warp * GS;
 
   if (cnt) {
@@ -866,6 +925,13 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
   // the barrier below
   fence_proxy_async_smem();
   produce_next(P, S);
+  // the round state the completion needs (read after the scan: fewer
+  // registers live across it)
+  cs.wlen = ld_cg_u32(&st->wlen);
+  cs.tiles = ld_cg_u32(&st->tiles);
+  cs.rounds = ld_cg_u32(&st->rounds);
+  const u32 ord = round_ord(P.cfg, cs.cur, cs.cend);
+  const u32 per_tile = max(1u, min(ceil_div(cs.wlen, DB), A_BLOCKS));
   __syncthreads();
   // with one item per tile (always so while A_BLOCKS is 1) the item
   // completes its tile and needs no completion counter
@@ -885,7 +951,7 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
   // predecessors' survivor counts, found by decoupled look-back over the
   // status words of the earlier tiles (all of which hold smaller tickets, so
   // every one of them is being or has been processed).
-  if (!P.cfg.ordered) {
+  if (ord == ORD_NONE) {
     // unordered compaction: the warp's slots from one atomic
     bool a[R];
     u32 m[R];
@@ -910,7 +976,7 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
       }
       base += __popc(m[r]);
     }
-  } else {
+  } else if (ord == ORD_LOOKBACK) {
   bool a[R];
   u32 bal[R];
   u32 wcount = 0;
@@ -980,7 +1046,7 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
   __threadfence();
   fence_proxy_async();
   __syncthreads();
-  if (!P.cfg.ordered) {
+  if (ord == ORD_NONE) {
     // one thread counts the tile and, for the phase's last tile, publishes
     // phase B: the other threads have nothing left to do in this item
     if (threadIdx.x == 0) {
@@ -1002,7 +1068,8 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
   }
   __syncthreads();
   if (!S.flag) return;
-  const u32 dl = S.tile_base;
+  // ORD_LAST: every tile's flags are final; the last one compacts the chunk
+  const u32 dl = ord == ORD_LAST ? compact_chunk<D>(sd, st, cs.cur, cs.cend, S) : S.tile_base;
   {
     // last tile of phase A: every tile has finished its look-back, so its
     // status word is free.  It now holds the dense tile's end for phase B:
@@ -1035,14 +1102,7 @@ __device__ void item_b(const Params& P, const SegDesc& sd, const Meta& mt, const
   const u32 s = mt.s;
   SegState* st = P.st + s;
   SegState cs;
-  cs.cend = ld_cg_u32(&st->cend);
-  cs.wlen = ld_cg_u32(&st->wlen);
   cs.dlen = ld_cg_u32(&st->dlen);
-  cs.rounds = ld_cg_u32(&st->rounds);
-  const u32 wb = ceil_div(cs.wlen, DB);
-  const u32 wbB = wb > A_BLOCKS ? wb - A_BLOCKS : 0;
-  const u32 dtiles = ceil_div(cs.dlen, TILE);
-  const u32 per_tile = wbB + ceil_div(cs.dlen, DB);
   const u32 dbase = mt.tile * TILE + warp * GS;
   const u32 cnt = mt.cnt;
   const DomSrc src = mt.dense ? DomSrc{sd.pts, sd.dpos, mt.base} : DomSrc{sd.win, nullptr, mt.base};
@@ -1061,6 +1121,16 @@ __device__ void item_b(const Params& P, const SegDesc& sd, const Meta& mt, const
   }
   fence_proxy_async_smem();  // as in item_a
   produce_next(P, S);
+  // the round state the completion needs (read after the scan, as in item_a)
+  cs.cur = ld_cg_u32(&st->cur);
+  cs.cend = ld_cg_u32(&st->cend);
+  cs.wlen = ld_cg_u32(&st->wlen);
+  cs.rounds = ld_cg_u32(&st->rounds);
+  const u32 ord = round_ord(P.cfg, cs.cur, cs.cend);
+  const u32 wb = ceil_div(cs.wlen, DB);
+  const u32 wbB = wb > A_BLOCKS ? wb - A_BLOCKS : 0;
+  const u32 dtiles = ceil_div(cs.dlen, TILE);
+  const u32 per_tile = wbB + ceil_div(cs.dlen, DB);
   __syncthreads();
   if (per_tile > 1) {
     if (threadIdx.x == 0) {
@@ -1120,7 +1190,7 @@ __device__ void item_b(const Params& P, const SegDesc& sd, const Meta& mt, const
     if (old == dtiles - 1) {
       // last dense tile: clear the tile ends for the next round's phase A,
       // then the next round
-      if (P.cfg.ordered) {
+      if (ord != ORD_NONE) {
         u32* stat = P.tstat + __ldcg(P.tbase + s);
         for (u32 j = 0; j < dtiles; ++j) stat[j] = 0;
       }

@@ -222,6 +222,9 @@ constexpr u32 DEFAULT_CHUNK_MIN = 1024;
 constexpr u32 DEFAULT_CHUNK_MAX = 262144;
 constexpr u32 DEFAULT_ALPHA_X4 = 32;
 constexpr u32 DEFAULT_DOM_BLOCK = 1024;
+enum : u32 { ORD_NONE = 0, ORD_LOOKBACK = 1, ORD_LAST = 2 };
+constexpr u32 ORD_LAST_MAX = 16384;
+
 // Default launch shape of the engine: warps per CTA x candidates per lane.
 constexpr u32 DEFAULT_ENGINE_WARPS = 4;
 constexpr u32 DEFAULT_ENGINE_CANDS = 4;
@@ -234,9 +237,15 @@ struct EngineCfg {
   // launch shape: warps per CTA (4 or 8) and candidates per lane (2 or 4);
   // 0 selects the default
   u32 warps, cands;
-  // 1: keep each segment's dense list in position order (look-back between
-  // tiles) so phase B tests only the lower-score half of the dense square;
-  // pays off for large chunks (the merge), costs waits for many small ones
+  // How phase A builds a segment's dense list: ORD_NONE in arrival order
+  // (phase B tests the whole dense square); ORD_LOOKBACK in position order,
+  // each tile writing its survivors at the sum of its predecessors' counts
+  // (decoupled look-back; phase B tests only the lower-score half of the
+  // square; pays off for large chunks, the merge); ORD_LAST in position
+  // order, written by the last tile of the phase over the whole chunk (the
+  // half square without look-back waits; for many small chunks: a round
+  // whose chunk is longer than ORD_LAST_MAX points uses ORD_NONE instead,
+  // since one CTA compacts the chunk)
   u32 ordered;
   // Test hooks, zero unless set through sky_diag_engine_wait_test: the bound
   // of every device-side wait without progress (0 = the built-in 4 s), and

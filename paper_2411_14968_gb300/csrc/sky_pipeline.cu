@@ -114,7 +114,8 @@ struct BatchBufs {
 };
 
 // Local-phase launches with at most this many segments keep ordered dense
-// lists (large chunks); launches with more compact in arrival order.
+// lists by look-back (large chunks); launches with more have the last tile
+// of each phase compact its chunk in order (many small chunks).
 constexpr u32 ORDERED_MAX_SEGS = 8;
 
 // word slots of Bufs::words
@@ -781,12 +782,13 @@ sky_status Runner::enqueue(BatchState& B) {
     // the engine's chunk policy of a shared launch is the first query's
     // a local phase with few segments has large chunks, like the merge
     CK(engine(bb.segs, persistent_segs, first_persistent->pl.cfg, first_persistent->b.words + W_ERR,
-              first_persistent->b.words + W_MAXROUND_LOCAL, persistent_segs <= ORDERED_MAX_SEGS));
+              first_persistent->b.words + W_MAXROUND_LOCAL,
+              persistent_segs <= ORDERED_MAX_SEGS ? ORD_LOOKBACK : ORD_LAST));
   }
   for (auto& w : ws) {
     if (w.q->n == 0 || w.pl.exec != SKY_EXEC_PLAIN) continue;
     for (u32 p = 0; p < w.pl.P; ++p)
-      CK(engine(bb.segs + w.seg_base + p, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_LOCAL, 1));
+      CK(engine(bb.segs + w.seg_base + p, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_LOCAL, ORD_LOOKBACK));
   }
   record(9, B);
   CK(fork());
@@ -855,10 +857,10 @@ sky_status Runner::enqueue(BatchState& B) {
         ++cnt;
       }
     if (first)
-      CK(engine(bb.msegs, cnt, first->pl.cfg, first->b.words + W_ERR, first->b.words + W_MAXROUND_MERGE, 1));
+      CK(engine(bb.msegs, cnt, first->pl.cfg, first->b.words + W_ERR, first->b.words + W_MAXROUND_MERGE, ORD_LOOKBACK));
     for (auto& w : ws)
       if (w.mseg >= 0 && w.pl.exec == SKY_EXEC_PLAIN)
-        CK(engine(bb.msegs + w.mseg, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_MERGE, 1));
+        CK(engine(bb.msegs + w.mseg, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_MERGE, ORD_LOOKBACK));
   }
   record(11, B);
   CK(fork());
