@@ -196,8 +196,11 @@ __device__ __forceinline__ bool in_pd(const NoSeqArgs& a, u32 i, u32 j) {
 // its images duplicated per word, word k = (image k, image k); dominators
 // are staged as pairs, word k = (image k of the first, image k of the
 // second), so one subtraction per attribute tests two dominators.
-constexpr int NR = 4;                // NoSeq candidates per lane
-constexpr int NGS = 32 * NR;         // candidates per NoSeq group
+// NoSeq candidates per lane: 4 above d = 4, where skylines are large and a
+// group's candidates mostly survive (more candidates share each staged
+// dominator); 2 up to d = 4, where most of u dies within a few dominators
+// and smaller groups leave earlier.
+__host__ __device__ constexpr int ns_r(int d) { return d <= 4 ? 2 : 4; }
 constexpr u32 INF2 = 0x7C007C00u;    // (+inf, +inf): a padding dominator fails every test
 constexpr u32 NEG_INF2 = 0xFC00FC00u;  // (-inf, -inf): a dead candidate passes no test
 
@@ -218,6 +221,7 @@ __device__ __forceinline__ u32 pair_fail(const u32 (&t)[D], const u32 (&w)[D]) {
 
 template <int D>
 struct NCand {
+  static constexpr int NR = ns_r(D);
   u32 t[NR][D];   // duplicated FP16 images (-inf when dead)
   u32 pos[NR];    // position in u
   bool alive[NR];
@@ -228,7 +232,7 @@ template <int D>
 __device__ __forceinline__ bool any_alive(const NCand<D>& c) {
   bool a = false;
 #pragma unroll
-  for (int r = 0; r < NR; ++r) a |= c.alive[r];
+  for (int r = 0; r < NCand<D>::NR; ++r) a |= c.alive[r];
   return a;
 }
 
@@ -236,7 +240,7 @@ __device__ __forceinline__ bool any_alive(const NCand<D>& c) {
 template <int D>
 __device__ __forceinline__ void ns_load(const NoSeqArgs& a, u32 base, u32 end, int lane, NCand<D>& c) {
 #pragma unroll
-  for (int r = 0; r < NR; ++r) {
+  for (int r = 0; r < NCand<D>::NR; ++r) {
     const u32 pos = base + r * 32 + lane;
     const bool ok = pos < end && ld_cg_u8(a.ualive + pos);
     const uint4 h = ok ? __ldg(a.uhc + pos) : make_uint4(0u, 0u, 0u, 0u);
@@ -303,10 +307,10 @@ __device__ void ns_scan_range(const NoSeqArgs& a, u32 lo, u32 hi, uint4* sp, NCa
       }
       u32 acc = 0xffffffffu;
 #pragma unroll
-      for (int r = 0; r < NR; ++r) acc &= pair_fail<D>(c.t[r], w);
+      for (int r = 0; r < NCand<D>::NR; ++r) acc &= pair_fail<D>(c.t[r], w);
       if ((acc & 0x80008000u) != 0x80008000u) {
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
+        for (int r = 0; r < NCand<D>::NR; ++r) {
           const u32 x = pair_fail<D>(c.t[r], w);
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
@@ -358,6 +362,7 @@ __global__ void __launch_bounds__(THREADS) k_noseq(NoSeqArgs a, const u32* __res
       }
       const u32 i = lo;
       const u32 ibeg = __ldg(a.useg + i), iend = __ldg(a.useg + i + 1);
+      constexpr u32 NGS = 32 * NCand<D>::NR;  // candidates per group
       const u32 base = ibeg + (G - __ldg(gpre + i)) * NGS;
       const u32 gend = min(base + NGS, iend);
       const float fmax = __ldg(a.uscore + gend - 1);
@@ -401,16 +406,16 @@ __global__ void __launch_bounds__(THREADS) k_noseq(NoSeqArgs a, const u32* __res
       }
       if (loaded) {
 #pragma unroll
-        for (int r = 0; r < NR; ++r)
+        for (int r = 0; r < NCand<D>::NR; ++r)
           if (c.was[r] && !c.alive[r]) a.ualive[c.pos[r]] = 0;
       }
     }
   }
 }
 
-__global__ void k_noseq_groups(const u32* __restrict__ useg, u32 P, u32* __restrict__ cnt) {
+__global__ void k_noseq_groups(const u32* __restrict__ useg, u32 P, u32 ngs, u32* __restrict__ cnt) {
   u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < P) cnt[i] = (useg[i + 1] - useg[i] + NGS - 1) / NGS;
+  if (i < P) cnt[i] = (useg[i + 1] - useg[i] + ngs - 1) / ngs;
 }
 
 // Segment descriptors of the local phase from the partition offsets;
@@ -506,7 +511,7 @@ cudaError_t launch_noseq(const NoSeqArgs& a, u32* gcnt, u32* gpre, u32* scan_tmp
                          cudaStream_t st) {
   if (a.P == 0) return cudaSuccess;
   note_launch();
-  k_noseq_groups<<<(a.P + 255) / 256, 256, 0, st>>>(a.useg, a.P, gcnt);
+  k_noseq_groups<<<(a.P + 255) / 256, 256, 0, st>>>(a.useg, a.P, 32u * ns_r(a.d), gcnt);
   cudaError_t e = scan_u32(gcnt, gpre, a.P, true, false, scan_tmp, st);
   if (e != cudaSuccess) return e;
   // gpre[P] = total groups
