@@ -230,3 +230,15 @@ def test_engine_launch_shape_rejected(ctx):
         with pytest.raises(native.SkylineError) as e:
             ctx.skyline(x, **bad)
         assert e.value.status == native.SKY_EINVAL
+
+
+# Local launches of more than eight segments keep each round's dense list in
+# score order by last-tile compaction while the round's chunk is at most 16k
+# points, and fall back to arrival order for longer chunks: segments of 25k
+# and 30k points reach both within one launch; both must give the oracle's
+# partitions, stage codes and skyline.
+def test_local_dense_list_modes(ctx, oracle_mod):
+    x = datagen.anticorrelated(300000, 5, 85)
+    _check(ctx, oracle_mod, x, "sliced", p=12)
+    _check(ctx, oracle_mod, x, "random", p=10, seed=4, rep="sorted")
+    _check(ctx, oracle_mod, x, "sliced", p=12, chunk_min=4096, chunk_alpha_x4=64)
