@@ -38,7 +38,7 @@
 //
 // Work queue.  Segments advance through their rounds independently; there
 // is no grid-wide barrier.  A phase of a segment is a task of items (tile of
-// 4 warps x 32 lanes x R candidates, dominator block of DB points, numbered
+// WARPS warps x 32 lanes x R candidates, dominator block of DB points, numbered
 // block-major so the strongest window points run first).  Publishing a task
 // reserves a contiguous range of tickets with one 64-bit atomic (task index
 // and ticket range together, so both orders agree) and then marks the task
