@@ -788,7 +788,8 @@ sky_status Runner::enqueue(BatchState& B) {
   for (auto& w : ws) {
     if (w.q->n == 0 || w.pl.exec != SKY_EXEC_PLAIN) continue;
     for (u32 p = 0; p < w.pl.P; ++p)
-      CK(engine(bb.segs + w.seg_base + p, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_LOCAL, ORD_LOOKBACK));
+      CK(engine(bb.segs + w.seg_base + p, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_LOCAL,
+                ORD_LOOKBACK));
   }
   record(9, B);
   CK(fork());
@@ -857,10 +858,12 @@ sky_status Runner::enqueue(BatchState& B) {
         ++cnt;
       }
     if (first)
-      CK(engine(bb.msegs, cnt, first->pl.cfg, first->b.words + W_ERR, first->b.words + W_MAXROUND_MERGE, ORD_LOOKBACK));
+      CK(engine(bb.msegs, cnt, first->pl.cfg, first->b.words + W_ERR, first->b.words + W_MAXROUND_MERGE,
+                ORD_LOOKBACK));
     for (auto& w : ws)
       if (w.mseg >= 0 && w.pl.exec == SKY_EXEC_PLAIN)
-        CK(engine(bb.msegs + w.mseg, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_MERGE, ORD_LOOKBACK));
+        CK(engine(bb.msegs + w.mseg, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_MERGE,
+                  ORD_LOOKBACK));
   }
   record(11, B);
   CK(fork());
