@@ -834,6 +834,19 @@ def ncu_case(which: str):
     (local phase, merge) of the second call are the captured ones."""
     import torch
     from paper_2411_14968_gb300 import datagen, native
+    if which == "noseq":
+        # one skewed query, N = 200k, d = 6, Angular (4,4,2,2,2) + Sorted
+        # reps, NoSeq final phase: the NoSeq kernel's profile case
+        x = datagen.skewed(200_000, 6, 4)
+        xt = torch.from_numpy(x).cuda()
+        with native.Context(0) as ctx:
+            p = native.make_params(scheme="angular", slices=[4, 4, 2, 2, 2], normalize=True, rep="sorted",
+                                   merge="noseq")
+            for _ in range(2):
+                r = ctx.skyline(xt, params=p)
+            torch.cuda.synchronize()
+            print(f"ncu case noseq: |Sky| = {r.shape[0]}, {ctx.stats()['launches']} launches per call")
+        return
     if which == "c3":
         # one 4M-point d = 8 quantised independent query, Grid m = 2 (256
         # cells): the workload where the memory-bound stages bound the query
@@ -874,10 +887,11 @@ def main():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--experiment", choices=["rep-filtering", "sweeps", "configs", "shapes", "fp16"], default=None,
                     help="run one of the paper's experiments instead of the benchmark")
-    ap.add_argument("--ncu-case", choices=["small", "batch", "c3"], default=None,
+    ap.add_argument("--ncu-case", choices=["small", "batch", "c3", "noseq"], default=None,
                     help="run a profiling case only, twice, default knobs, no timing: 'small' = one query "
                          "(anticorrelated N=200k, d=6, Sliced p=64); 'batch' = the benchmark's batched step; "
-                         "'c3' = one quantised independent query, N=4M, d=8, Grid m=2")
+                         "'c3' = one quantised independent query, N=4M, d=8, Grid m=2; 'noseq' = one skewed "
+                         "query, N=200k, d=6, Angular (4,4,2,2,2) + Sorted reps, NoSeq")
     # FP32 compare peak in T compares/s; 0 derives it from the device's SM
     # count x 64 compare lanes per SM per clock x the maximum SM clock seen
     ap.add_argument("--compare-peak-tcmp", type=float, default=0.0)
