@@ -23,6 +23,8 @@ import platform
 import sys
 import time
 
+import numpy as np
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
@@ -49,6 +51,26 @@ WORKLOADS = {
 }
 
 
+def noseq_score_cut_minimum(x, r):
+    """The fewest tests any exact NoSeq with the score cut makes (Section
+    4.2 with pd_i = u minus u_i, Random / Angular): a surviving tuple t must
+    be tested against every s in pd_i with score(s) <= score(t), and a
+    dropped one at least once.  From the oracle's own partitions and stage
+    codes; scores are the oracle's left-to-right FP32 sums."""
+    st, pid = r["stage"], r["pid"]
+    inu = (st == O.ST_SKY) | (st == O.ST_MERGE)
+    f = O.scores(x)
+    fu, pu, sky = f[inu], pid[inu], st[inu] == O.ST_SKY
+    order = np.sort(fu)
+    total = 0
+    for part in np.unique(pu):
+        own = np.sort(fu[pu == part])
+        t = fu[(pu == part) & sky]
+        total += int((np.searchsorted(order, t, side="right") - np.searchsorted(own, t, side="right")).sum())
+    total += int((~sky).sum())
+    return {"merge_tests_score_cut_min": total}
+
+
 def main(names):
     for wl in names or WORKLOADS:
         run(wl)
@@ -66,6 +88,7 @@ def run(wl):
         out["variants"][name] = {
             "local_tests": r["tests"][0],
             "merge_tests": r["tests"][1],
+            **(noseq_score_cut_minimum(x, r) if kw.get("merge") == O.MERGE_NOSEQ else {}),
             "skyline": int(r["indices"].shape[0]),
             "local_union": int(((st == O.ST_SKY) | (st == O.ST_MERGE)).sum()),
             "oracle_seconds": round(time.time() - t, 1),
