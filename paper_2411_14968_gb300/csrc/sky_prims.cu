@@ -351,6 +351,86 @@ __global__ void k_sort_pass(const u64* __restrict__ kin, const u32* __restrict__
   }
 }
 
+// Inputs of at most SMALL_SORT_MAX keys are latency-bound: one block sorts
+// them with the same stable LSD passes in one launch instead of two plus one
+// per pass.  The keys and values of a pass are read from shared memory; the
+// pass scatters them into the other global buffer of the pair (L2-resident
+// at this size) and the next pass loads them back.  Warp w owns the
+// elements [w * per, (w + 1) * per) in lane-strided order, so (warp,
+// iteration, lane) is the input order, as in k_sort_pass, and the
+// permutation is the same.
+constexpr u32 SMALL_SORT_MAX = 4096;
+constexpr size_t SMALL_DSMEM = (size_t)SMALL_SORT_MAX * (sizeof(u64) + sizeof(u32));
+
+__global__ void __launch_bounds__(RT) k_sort_small(u64* k0, u64* k1, u32* v0, u32* v1, u64 n,
+                                                   const u32* __restrict__ n_dev, int lo_bit, int npass,
+                                                   int last_bits) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  __shared__ u32 s_w[RT / 32][RT];  // per-warp digit counts, then per-warp digit starts
+  __shared__ u32 s_start[RT];       // start of each digit in the output
+  __shared__ u32 s_sc[32];
+  u64* ks = reinterpret_cast<u64*>(s_dyn);
+  u32* vs = reinterpret_cast<u32*>(ks + SMALL_SORT_MAX);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const u32 lt = (1u << lane) - 1u;
+  const u32 m = (u32)radix_count(n, n_dev);
+  // elements per warp, a multiple of 32 so every lane runs the same loop
+  const u32 per = (m + RT - 1) / RT * 32;
+  const u32 wb = warp * per;
+  for (int p = 0; p < npass; ++p) {
+    // pass p reads buffer p % 2 and writes buffer (p + 1) % 2
+    const u64* kin = (p & 1) ? k1 : k0;
+    const u32* vin = (p & 1) ? v1 : v0;
+    u64* kout = (p & 1) ? k0 : k1;
+    u32* vout = (p & 1) ? v0 : v1;
+    for (u32 i = tid; i < m; i += RT) {
+      ks[i] = kin[i];
+      vs[i] = vin[i];
+    }
+    const int shift = lo_bit + 8 * p;
+    const u32 mask = p == npass - 1 ? (1u << last_bits) - 1u : 0xffu;
+#pragma unroll
+    for (int w = 0; w < RT / 32; ++w) s_w[w][tid] = 0;
+    __syncthreads();
+    for (u32 it = 0; it < per; it += 32) {
+      const u32 e = wb + it + lane;
+      const bool valid = e < m;
+      const u32 dg = valid ? (u32)(ks[e] >> shift) & mask : 0xffffffffu;
+      const u32 peers = __match_any_sync(FULL, dg);
+      if (valid && lane == __ffs(peers) - 1) s_w[warp][dg] += __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    u32 c = 0;
+#pragma unroll
+    for (int w = 0; w < RT / 32; ++w) {
+      const u32 cw = s_w[w][tid];
+      s_w[w][tid] = c;
+      c += cw;
+    }
+    u32 agg;
+    s_start[tid] = block_scan_incl(c, s_sc, &agg, OpAdd()) - c;
+    __syncthreads();
+    for (u32 it = 0; it < per; it += 32) {
+      const u32 e = wb + it + lane;
+      const bool valid = e < m;
+      const u64 key = valid ? ks[e] : 0ull;
+      const u32 dg = valid ? (u32)(key >> shift) & mask : 0xffffffffu;
+      const u32 peers = __match_any_sync(FULL, dg);
+      if (valid) {
+        const u32 pos = s_start[dg] + s_w[warp][dg] + __popc(peers & lt);
+        kout[pos] = key;
+        vout[pos] = vs[e];
+      }
+      __syncwarp();
+      if (valid && lane == __ffs(peers) - 1) s_w[warp][dg] += __popc(peers);
+      __syncwarp();
+    }
+    // the next pass reloads the buffer the block has just written
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 size_t scan_tmp_words(u64 n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE) + 2; }
@@ -379,6 +459,15 @@ cudaError_t radix_sort(u64* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32*
   const int npass = (bits + 7) / 8;
   if (npass > MAX_PASS || n >= (1ull << 32)) return cudaErrorInvalidValue;
   const int last_bits = bits - 8 * (npass - 1);
+  if (n <= SMALL_SORT_MAX) {
+    cudaError_t e = cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SMALL_DSMEM);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    k_sort_small<<<1, RT, SMALL_DSMEM, st>>>(k[0], k[1], v[0], v[1], n, n_dev, lo_bit, npass, last_bits);
+    *out_sel = npass & 1;  // the last pass wrote buffer npass % 2
+    return cudaGetLastError();
+  }
   const u64 nb = (n + RTILE - 1) / RTILE;
   u32* ghist = work + W_GHIST;
   u32* ctr = work + W_CTR;
