@@ -119,11 +119,56 @@ __global__ void k_scan_down(const In* __restrict__ in, u32* __restrict__ out, u6
   }
 }
 
+// Scans of at most SCAN_SMALL_MAX elements (latency-bound): one block walks
+// the tiles in order with a running carry, in one launch instead of three;
+// the total goes to the same word as in the three-kernel scan.  In-place
+// use is safe: a thread reads its elements before the block writes any.
+constexpr u64 SCAN_SMALL_MAX = 8 * SCAN_TILE;
+
+template <class In, class Op>
+__global__ void k_scan_small(const In* in, u32* out, u64 n, u32* total, bool exclusive) {
+  __shared__ u32 sh[32];
+  __shared__ u32 buf[SCAN_T];
+  Op op;
+  u32 carry = Op::identity;
+  for (u64 b0 = 0; b0 < n; b0 += SCAN_TILE) {
+    const u64 base = b0 + (u64)threadIdx.x * SCAN_IPT;
+    u32 v[SCAN_IPT];
+    u32 acc = Op::identity;
+#pragma unroll
+    for (int i = 0; i < SCAN_IPT; ++i) {
+      const u64 e = base + i;
+      v[i] = e < n ? (u32)in[e] : Op::identity;
+      acc = op(acc, v[i]);
+    }
+    u32 agg;
+    const u32 inc = block_scan_incl(acc, sh, &agg, op);
+    buf[threadIdx.x] = inc;
+    __syncthreads();
+    u32 run = op(carry, threadIdx.x > 0 ? buf[threadIdx.x - 1] : Op::identity);
+#pragma unroll
+    for (int i = 0; i < SCAN_IPT; ++i) {
+      const u64 e = base + i;
+      const u32 nxt = op(run, v[i]);
+      if (e < n) out[e] = exclusive ? run : nxt;
+      run = nxt;
+    }
+    carry = op(carry, agg);
+    __syncthreads();  // buf is rewritten by the next tile
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
 template <class In, class Op>
 cudaError_t scan_impl(const In* in, u32* out, u64 n, bool exclusive, u32* tmp, cudaStream_t st) {
   u64 nb = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (nb == 0) {
     return cudaMemsetAsync(tmp, 0, sizeof(u32), st);
+  }
+  if (n <= SCAN_SMALL_MAX) {
+    note_launch();
+    k_scan_small<In, Op><<<1, SCAN_T, 0, st>>>(in, out, n, tmp + nb, exclusive);
+    return cudaGetLastError();
   }
   note_launch();
   k_scan_reduce<In, Op><<<(unsigned)nb, SCAN_T, 0, st>>>(in, n, tmp);
