@@ -782,6 +782,56 @@ def shapes_experiment(local: int):
     print(json.dumps({"experiment": "engine launch shapes on the batched step", "rows": rows}), flush=True)
 
 
+VALUE_RANGES = [
+    ("unit [0,1]", 1.0, 0.0),
+    ("offset +1024", 1.0, 1024.0),
+    ("scaled x2^17", 2.0 ** 17, 0.0),
+    ("scaled x2^-20", 2.0 ** -20, 0.0),
+]
+
+
+def value_range_experiment(local: int):
+    """The batched step (the benchmark's four queries on one input) on the
+    benchmark's anticorrelated points moved into other value ranges (scaled
+    by a power of two, which keeps every comparison; or offset, where FP32
+    rounding makes some values equal), with the FP16 images of the values
+    and with the rank images (sky_rank_space): device time of the batch and
+    of its two engine launches, median of 7 runs.  Each range's skyline is
+    checked against the oracle once (its threaded Algorithm 2: Sliced p=64
+    with the NoSeq merge, whose skyline equals sequential SFS's)."""
+    import torch
+    from paper_2411_14968_gb300 import datagen, native
+    from oracle import oracle as O
+    O.set_threads(os.cpu_count() or 1)
+    x0 = datagen.anticorrelated(N, D, SEED)
+    rows = []
+    with native.Context(local) as ctx:
+        ctx.set_timing(True)
+        for name, scale, offset in VALUE_RANGES:
+            x = np.ascontiguousarray(x0 * np.float32(scale) + np.float32(offset), dtype=np.float32)
+            want = O.partitioned(x, scheme=O.SLICED, p=64, merge=O.MERGE_NOSEQ)["indices"]
+            xt = torch.from_numpy(x).cuda()
+            for images in ("values", "ranks"):
+                ps = [native.make_params(images=images, **kw) for _, kw in VARIANTS]
+                for _ in range(2):
+                    got = ctx.skyline_batch([(xt, p) for p in ps])
+                for g in got:
+                    assert np.array_equal(g.cpu().numpy().astype(np.uint32), want), (name, images)
+                sts = []
+                for _ in range(7):
+                    ctx.skyline_batch([(xt, p) for p in ps])
+                    sts.append(ctx.stats())
+                med = lambda k: statistics.median(st[k] for st in sts)  # noqa: E731
+                rows.append({"values": name, "images": images, "skyline": int(want.shape[0]),
+                             "ms_total": round(med("ms_total"), 3), "ms_prep": round(sts[0]["ms_phase"][0], 3),
+                             "ms_dom_local": round(med("ms_dom_local"), 3),
+                             "ms_dom_merge": round(med("ms_dom_merge"), 3),
+                             "points_per_s": len(VARIANTS) * N / (med("ms_total") * 1e-3)})
+                print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"experiment": "value ranges: FP16 images of the values vs rank images", "rows": rows}),
+          flush=True)
+
+
 def fp16_images(x):
     """Round-down FP16 images of FP32 values, clamped to the finite FP16
     range (the images the dominance kernels test first)."""
@@ -886,7 +936,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--experiment", choices=["rep-filtering", "sweeps", "configs", "shapes", "fp16"], default=None,
+    ap.add_argument("--experiment", choices=["rep-filtering", "sweeps", "configs", "shapes", "fp16", "value-range"],
+                    default=None,
                     help="run one of the paper's experiments instead of the benchmark")
     ap.add_argument("--ncu-case", choices=["small", "batch", "c3", "noseq"], default=None,
                     help="run a profiling case only, twice, default knobs, no timing: 'small' = one query "
@@ -916,6 +967,9 @@ def main():
         return
     if args.experiment == "fp16":
         fp16_experiment()
+        return
+    if args.experiment == "value-range":
+        value_range_experiment(local)
         return
     if args.impl == "reference":
         reference_arm(args, rank, world)

@@ -73,6 +73,23 @@ typedef enum {
   SKY_EXEC_PLAIN = 1       /* one launch per partition, in partition order */
 } sky_exec;
 
+/* The 16-bit images the dominance engine tests before its FP32 test (a
+   filter that never changes a result, only how many pairs reach the FP32
+   test; Def. 1 is invariant under any strictly increasing map of each
+   attribute, and the images need only be non-decreasing):
+   SKY_IMAGES_VALUES: each attribute rounded down to FP16 (clamped to the
+     finite FP16 range).  Free, and sharp for values of moderate magnitude
+     spread over many FP16 steps (e.g. [0, 1]); blunt when a column's values
+     share few FP16 numbers -- a large common offset, magnitudes above
+     65504 or below about 1e-5 -- and the engine then runs several times
+     slower (every pair reaches the FP32 test).
+   SKY_IMAGES_RANKS: each attribute's dense rank in its column (sky_rank_space),
+     used as an order-preserving 15-bit code: exact (distinct values keep
+     distinct codes) for columns of at most 31,744 distinct values, scaled
+     down otherwise.  Costs one sort per attribute; the engine's speed then
+     no longer depends on the value range. */
+typedef enum { SKY_IMAGES_VALUES = 0, SKY_IMAGES_RANKS = 1 } sky_images;
+
 typedef struct {
   uint32_t struct_size;        /* sizeof(sky_params); filled by sky_params_init */
   sky_partitioning scheme;
@@ -95,6 +112,7 @@ typedef struct {
   uint32_t engine_warps;       /* warps per CTA of the engine's work items: 4 or 8 (default 4) */
   uint32_t engine_cands;       /* candidates per lane: 2 or 4 (default 4); a work item's tile is
                                   32 x engine_warps x engine_cands candidates */
+  sky_images images;           /* images of the engine's first test (default SKY_IMAGES_VALUES) */
 } sky_params;
 
 /* Per-call statistics (sky_get_stats). */
@@ -288,6 +306,28 @@ sky_status sky_wait(sky_ctx* ctx, uint64_t ticket, uint32_t* out_idx, uint64_t* 
 /* Runs the queued queries to completion and stops the workers (their
    workspaces are freed).  Uncollected tickets stay collectable. */
 sky_status sky_serve_stop(sky_ctx* ctx);
+
+/* Rank space of a point set (Def. 1 compares each attribute only by order,
+   so replacing every value by its rank in its column keeps every dominance
+   relation and the skyline).  points: N x d FP32 row-major (host or
+   device); -0.0 and +0.0 are one value.  Outputs (each may be NULL; host or
+   device):
+     out_ranks[i*d + a]  dense rank of points[i*d + a] in column a: the
+                         number of distinct values of column a below it
+                         (0 .. distinct - 1; equal values, equal ranks);
+     out_distinct[a]     number of distinct values of column a;
+     out_codes[i*d + a]  the 15-bit code that SKY_IMAGES_RANKS gives the
+                         engine: the rank itself when the column has at most
+                         31,744 distinct values, else floor(rank x 31,743 /
+                         (distinct - 1)); read as the bits of an FP16
+                         number, the codes are finite, non-negative and
+                         non-decreasing in the value.
+   Blocks until the outputs are written.  Errors: SKY_EINVAL for d outside
+   1..8, N >= 2^32 - 1, NULL points with N > 0, memory of another GPU, or a
+   NaN attribute; SKY_ENOMEM; SKY_ECUDA.  N = 0 writes only out_distinct
+   (zeros). */
+sky_status sky_rank_space(sky_ctx* ctx, const float* points, uint64_t n, uint32_t d, uint32_t* out_ranks,
+                          uint32_t* out_distinct, uint16_t* out_codes);
 
 /* Statistics of a call.  ticket_or_0 = 0: the last completed sky_skyline,
    sky_skyline_ex or sky_skyline_batch call of the context (a batch's sizes

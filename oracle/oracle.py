@@ -66,6 +66,7 @@ def _load():
         lib.orc_skyline_brute.argtypes = [P, i64, i32, P]
         lib.orc_relative_skyline.argtypes = [P, i64, P, i64, i32, P]
         lib.orc_scores.argtypes = [P, i64, i32, P]
+        lib.orc_dense_ranks.argtypes = [P, i64, i32, P, P]
         lib.orc_sfs_all.argtypes = [P, i64, i32, P, P]
         lib.orc_sfs_all.restype = i64
         lib.orc_key_scale.argtypes = [P, i64, i32, P]
@@ -122,6 +123,17 @@ def relative_skyline(r, c) -> np.ndarray:
     if r.shape[0]:
         _load().orc_relative_skyline(_ptr(r), r.shape[0], _ptr(c), c.shape[0], r.shape[1], _ptr(out))
     return out.astype(bool)
+
+
+def dense_ranks(points):
+    """Rank space (Def. 1 compares attributes only by order): returns
+    (ranks uint32 [N, d], distinct uint32 [d]), ranks[i, a] = the number of
+    distinct values of column a below points[i, a] (-0.0 == +0.0)."""
+    p = _pts(points)
+    ranks = np.zeros(p.shape, dtype=np.uint32)
+    distinct = np.zeros(p.shape[1], dtype=np.uint32)
+    _load().orc_dense_ranks(_ptr(p), p.shape[0], p.shape[1], _ptr(ranks), _ptr(distinct))
+    return ranks, distinct
 
 
 def scores(points) -> np.ndarray:

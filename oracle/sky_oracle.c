@@ -100,6 +100,40 @@ void orc_relative_skyline(const float *r, int64_t nr, const float *c, int64_t nc
   }
 }
 
+/* --------------------------------------------------- rank space (from Def. 1) */
+
+/* Def. 1 looks at each attribute of two tuples only through <= and <, so
+   replacing every value of column a by its dense rank in that column (the
+   number of distinct values of the column below it) keeps every dominance
+   relation.  ranks[i*d + a] = that rank (-0.0 and +0.0 are one value);
+   distinct[a] = the column's number of distinct values. */
+static int cmp_float(const void *a, const void *b) {
+  const float x = *(const float *)a, y = *(const float *)b;
+  return (x < y) ? -1 : (x > y);
+}
+
+void orc_dense_ranks(const float *pts, int64_t n, int d, uint32_t *ranks, uint32_t *distinct) {
+  float *col = (float *)malloc((size_t)(n > 0 ? n : 1) * sizeof(float));
+  for (int a = 0; a < d; ++a) {
+    for (int64_t i = 0; i < n; ++i) col[i] = pts[i * d + a] + 0.0f;
+    qsort(col, (size_t)n, sizeof(float), cmp_float);
+    int64_t m = 0; /* the distinct values, ascending, in col[0..m) */
+    for (int64_t i = 0; i < n; ++i)
+      if (m == 0 || col[i] != col[m - 1]) col[m++] = col[i];
+    distinct[a] = (uint32_t)m;
+    for (int64_t i = 0; i < n; ++i) {
+      const float v = pts[i * d + a] + 0.0f;
+      int64_t lo = 0, hi = m; /* first position holding a value >= v */
+      while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (col[mid] < v) lo = mid + 1; else hi = mid;
+      }
+      ranks[i * d + a] = (uint32_t)lo;
+    }
+  }
+  free(col);
+}
+
 /* ------------------------------------------------- §2 monotone scoring function */
 
 static float score_of(const float *t, int d) {

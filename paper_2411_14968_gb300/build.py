@@ -21,7 +21,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libskyline.so")
 SOURCES = ["sky_engine_w4r4.cu", "sky_engine_w8r4.cu", "sky_engine_w4r2.cu", "sky_engine_w8r2.cu", "sky_api.cu",
            "sky_dom.cu", "sky_engine.cu", "sky_prep.cu", "sky_pipeline.cu", "sky_prims.cu", "sky_probe.cu",
-           "sky_serve.cu", "sky_static.cu", "sky_tune.cu"]
+           "sky_rank.cu", "sky_serve.cu", "sky_static.cu", "sky_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC,-O2",
          "-I", os.path.join(ROOT, "include")]

@@ -72,6 +72,7 @@ void sky_params_init(sky_params* p) {
   p->reps_per_partition = 1;
   p->merge = SKY_MERGE_SEQUENTIAL;
   p->exec = SKY_EXEC_PERSISTENT;
+  p->images = SKY_IMAGES_VALUES;
 }
 
 sky_status sky_create(sky_ctx** ctx, int device, size_t mem_budget_bytes) {
@@ -138,6 +139,12 @@ void sky_serve_config_init(sky_serve_config* cfg) {
   cfg->struct_size = sizeof(sky_serve_config);
   cfg->workers = 2;
   cfg->max_batch = 64;
+}
+
+sky_status sky_rank_space(sky_ctx* ctx, const float* points, uint64_t n, uint32_t d, uint32_t* out_ranks,
+                          uint32_t* out_distinct, uint16_t* out_codes) {
+  if (!ctx) return SKY_EINVAL;
+  return ctx->run.rank_space(points, n, d, out_ranks, out_distinct, reinterpret_cast<unsigned short*>(out_codes));
 }
 
 uint64_t sky_query_bytes(uint64_t n, uint32_t d, const sky_params* params) {

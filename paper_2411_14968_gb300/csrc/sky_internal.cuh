@@ -96,6 +96,30 @@ size_t radix_work_words(u64 n);
 cudaError_t radix_sort(u64* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32* work, cudaStream_t st,
                        int* out_sel, const u32* n_dev = nullptr, u32* err = nullptr);
 
+// ---------------------------------------------------------------- rank space (sky_rank.cu)
+// Codes of the rank images: the finite non-negative FP16 bit patterns
+// 0x0000..0x7BFF, in increasing order.
+constexpr u32 RANK_CODES = 0x7C00;
+// Order-preserving code of dense rank `rank` in a column of R distinct
+// values: the rank itself when it fits, else rank scaled down (floor), which
+// is non-decreasing in the rank and maps R - 1 to the largest code.
+__host__ __device__ inline u32 rank_code(u32 rank, u32 R) {
+  return R <= RANK_CODES ? rank : (u32)(((u64)rank * (RANK_CODES - 1)) / (R - 1));
+}
+struct RankScratch {
+  u64* keys[2];   // n each
+  u32* vals[2];   // n each
+  u32* work;      // radix_work_words(n)
+  u8* flag;       // n
+  u32* incl;      // n
+  u32* scan_tmp;  // scan_tmp_words(n)
+};
+// Dense ranks of every column of X (N x d row-major, device): ranks[i*d + a]
+// (optional), codes[i*code_stride + a] = rank_code(rank, distinct[a])
+// (optional), distinct[a] (optional, device).  NaN sets ERR_NAN in *err.
+cudaError_t launch_rank_space(const float* X, u64 n, u32 d, const RankScratch& s, u32* ranks,
+                              unsigned short* codes, u32 code_stride, u32* distinct, u32* err, cudaStream_t st);
+
 // ---------------------------------------------------------------- prep (sky_prep.cu)
 struct PrepArgs {
   const float* X;        // row-major input, n x d
@@ -120,7 +144,8 @@ struct GatherArgs {
   const u32* vals;       // sorted point indices
   u32 P;                 // partitions
   float* pts;            // out: padded points in sorted order, vec_of(d) float4 each
-  uint4* hc;             // out: FP16 images of the points
+  const uint4* rcode;    // rank images by original index (rank space), or NULL: FP16 round-down
+  uint4* hc;             // out: images of the points (rcode's, else FP16 round-down)
   float* score;          // out: scores in sorted order
   u32* orig;             // out: original index of sorted position
   u32* spid;             // out: partition of sorted position

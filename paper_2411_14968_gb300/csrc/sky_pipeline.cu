@@ -47,6 +47,7 @@ struct Plan {
   u32 k = 1;
   int merge = 0;
   int exec = 0;
+  int images = SKY_IMAGES_VALUES;
   EngineCfg cfg{};
   int pid_bits = 0;
   bool x_on_host = false;
@@ -224,6 +225,8 @@ sky_status validate(const float* points, u64 n, u32 d, const sky_params* pa, Pla
   pl->merge = (int)p.merge;
   if (p.exec != SKY_EXEC_PERSISTENT && p.exec != SKY_EXEC_PLAIN) return bad("unknown exec");
   pl->exec = (int)p.exec;
+  if (p.images != SKY_IMAGES_VALUES && p.images != SKY_IMAGES_RANKS) return bad("unknown images mode");
+  pl->images = (int)p.images;
   u64 P = 1;
   switch (p.scheme) {
     case SKY_GRID:
@@ -657,6 +660,15 @@ sky_status Runner::enqueue(BatchState& B) {
     // Region representatives
     if (pr.normalize || (pl.normalize && pl.rep == SKY_REP_REGION))
       CK(launch_colmax(w.X, n, D, b.words + W_COLMAX, err, st));
+    // rank images (by original index) in the union's image buffer, which is
+    // free until the local phase ends; keys, values, mask and head are
+    // rewritten by the prep and the sorts below
+    if (pl.images == SKY_IMAGES_RANKS) {
+      CK(cudaMemsetAsync(b.uhc, 0, n * sizeof(uint4), st));
+      RankScratch rs{{b.keys[0], b.keys[1]}, {b.vals[0], b.vals[1]}, b.hist, b.mask, b.head, b.scan_tmp};
+      CK(launch_rank_space(w.X, n, (u32)D, rs, nullptr, reinterpret_cast<unsigned short*>(b.uhc), 8, nullptr,
+                           err, st));
+    }
     CK(launch_prep(pr, D, st));
     int sel = 0;
     if (pl.scheme == SCHEME_RANDOM || pl.scheme == SCHEME_SLICED) {
@@ -685,6 +697,7 @@ sky_status Runner::enqueue(BatchState& B) {
     ga.vals = b.vals[sel];
     ga.P = pl.P;
     ga.pts = b.pts;
+    ga.rcode = pl.images == SKY_IMAGES_RANKS ? b.uhc : nullptr;
     ga.hc = b.hc;
     ga.score = b.score;
     ga.orig = b.orig;

@@ -78,6 +78,11 @@ class Runner {
   sky_status enqueue(BatchState& B);
   sky_status finish(BatchState& B);
 
+  // sky_rank_space: dense ranks, distinct counts and rank codes of every
+  // column (each output optional; host or device).  Blocks.
+  sky_status rank_space(const float* points, u64 n, u32 d, u32* out_ranks, u32* out_distinct,
+                        unsigned short* out_codes);
+
   // Workspace bytes a query of this shape needs (for admission control).
   static size_t query_bytes(u64 n, u32 d, const sky_params* params);
 

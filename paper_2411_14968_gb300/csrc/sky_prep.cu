@@ -226,7 +226,7 @@ __global__ void k_gather(GatherArgs g) {
   float4* dst = reinterpret_cast<float4*>(g.pts) + r * V;
   dst[0] = make_float4(x[0], x[1], x[2], x[3]);
   if (V > 1) dst[1] = make_float4(x[4], x[5], x[6], x[7]);
-  g.hc[r] = fp16_codes(x);
+  g.hc[r] = g.rcode ? g.rcode[i] : fp16_codes(x);
   g.score[r] = score_of<D>(x);
   g.orig[r] = i;
   g.alive[r] = 1;

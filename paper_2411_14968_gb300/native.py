@@ -21,6 +21,8 @@ SCHEMES = {"random": 0, "grid": 1, "angular": 2, "sliced": 3, "none": 4}
 REPS = {"none": 0, "sorted": 1, "region": 2}
 MERGES = {"sequential": 0, "noseq": 1}
 EXECS = {"persistent": 0, "plain": 1}
+IMAGES = {"values": 0, "ranks": 1}
+RANK_CODES = 0x7C00  # codes of the rank images: 0 .. RANK_CODES - 1
 STAGE_SKY, STAGE_GRID, STAGE_REP, STAGE_LOCAL, STAGE_MERGE = 1, 2, 3, 4, 5
 
 
@@ -44,6 +46,7 @@ class SkyParams(ctypes.Structure):
         ("dom_block", ctypes.c_uint32),
         ("engine_warps", ctypes.c_uint32),
         ("engine_cands", ctypes.c_uint32),
+        ("images", ctypes.c_int),
     ]
 
 
@@ -107,7 +110,8 @@ EXPORTS = ["sky_params_init", "sky_create", "sky_set_stream", "sky_set_timing", 
            "sky_skyline_ex", "sky_get_stats", "sky_status_str", "sky_last_error", "sky_destroy",
            "sky_probe_compare_rate", "sky_skyline_static", "sky_skyline_batch", "sky_serve_config_init", "sky_query_bytes",
            "sky_serve_start", "sky_submit", "sky_poll", "sky_wait", "sky_serve_stop", "sky_autotune", "sky_autotune_batch",
-           "sky_graph_capture", "sky_graph_launch", "sky_graph_destroy", "sky_diag_engine_wait_test"]
+           "sky_graph_capture", "sky_graph_launch", "sky_graph_destroy", "sky_diag_engine_wait_test",
+           "sky_rank_space"]
 
 _lock = threading.Lock()
 _lib = None
@@ -184,9 +188,11 @@ def load(build_if_missing: bool = True):
         L.sky_serve_stop.argtypes = [P]
         L.sky_serve_stop.restype = i32
         L.sky_skyline_static.argtypes = [P, u64, u32, P, ctypes.POINTER(u64), P]
+        L.sky_skyline_static.restype = i32
         L.sky_diag_engine_wait_test.argtypes = [P, u64, u32]
         L.sky_diag_engine_wait_test.restype = i32
-        L.sky_skyline_static.restype = i32
+        L.sky_rank_space.argtypes = [P, P, u64, u32, P, P, P]
+        L.sky_rank_space.restype = i32
         _lib = L
         return L
 
@@ -194,7 +200,7 @@ def load(build_if_missing: bool = True):
 def make_params(scheme="none", p: int = 1, slices=None, normalize=False, slice_dim=0, seed=0,
                 grid_filter=True, rep="none", reps_per_partition=1, merge="sequential",
                 exec="persistent", chunk_min=0, chunk_max=0, chunk_alpha_x4=0, dom_block=0,
-                engine_warps=0, engine_cands=0) -> SkyParams:
+                engine_warps=0, engine_cands=0, images="values") -> SkyParams:
     L = load()
     sp = SkyParams()
     L.sky_params_init(ctypes.byref(sp))
@@ -214,6 +220,7 @@ def make_params(scheme="none", p: int = 1, slices=None, normalize=False, slice_d
     sp.chunk_min, sp.chunk_max = int(chunk_min), int(chunk_max)
     sp.chunk_alpha_x4, sp.dom_block = int(chunk_alpha_x4), int(dom_block)
     sp.engine_warps, sp.engine_cands = int(engine_warps), int(engine_cands)
+    sp.images = IMAGES[images] if isinstance(images, str) else int(images)
     return sp
 
 
@@ -279,6 +286,40 @@ class Context:
         s = SkyStats()
         self._check(self._L.sky_get_stats(self._h, int(ticket), ctypes.byref(s)))
         return s.as_dict()
+
+    def rank_space(self, points):
+        """Dense ranks of every column (sky_rank_space): returns (ranks
+        uint32 [N, d], distinct uint32 [d], codes uint16 [N, d]) -- numpy
+        arrays for host input, CUDA torch tensors (int32, int32, int16
+        holding the same bits) for a CUDA tensor."""
+        if _is_cuda_tensor(points):
+            import torch
+            if points.dtype != torch.float32 or points.dim() != 2:
+                raise ValueError("points must be a float32 [N, d] tensor")
+            points = points.contiguous()
+            n, d = points.shape
+            self.set_stream(torch.cuda.current_stream(points.device).cuda_stream)
+            ranks = torch.empty((max(n, 1), d), dtype=torch.int32, device=points.device)
+            distinct = torch.empty(d, dtype=torch.int32, device=points.device)
+            codes = torch.empty((max(n, 1), d), dtype=torch.int16, device=points.device)
+            self._check(self._L.sky_rank_space(self._h, ctypes.c_void_p(points.data_ptr()), n, d,
+                                               ctypes.c_void_p(ranks.data_ptr()),
+                                               ctypes.c_void_p(distinct.data_ptr()),
+                                               ctypes.c_void_p(codes.data_ptr())))
+            return ranks[:n], distinct, codes[:n]
+        a = np.ascontiguousarray(points, dtype=np.float32)
+        if a.ndim != 2:
+            raise ValueError("points must be [N, d]")
+        n, d = a.shape
+        self.set_stream(0)
+        ranks = np.zeros((max(n, 1), d), dtype=np.uint32)
+        distinct = np.zeros(d, dtype=np.uint32)
+        codes = np.zeros((max(n, 1), d), dtype=np.uint16)
+        self._check(self._L.sky_rank_space(self._h, a.ctypes.data_as(ctypes.c_void_p), n, d,
+                                           ranks.ctypes.data_as(ctypes.c_void_p),
+                                           distinct.ctypes.data_as(ctypes.c_void_p),
+                                           codes.ctypes.data_as(ctypes.c_void_p)))
+        return ranks[:n], distinct, codes[:n]
 
     def skyline(self, points, params: SkyParams | None = None, out=None, with_diag: bool = False, **kw):
         """Sky(points): ascending indices of the non-dominated points.

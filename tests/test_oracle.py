@@ -514,3 +514,47 @@ def test_key_scale_column_max(oracle_mod):
     assert oracle_mod.key_scale(x).tolist() == [4.0, 1.0, 1.0]
     g = oracle_mod.assign_grid(np.array([[2.0, 0.0, 0.0]], np.float32), [2, 2, 2], normalize=False)
     assert g.tolist() == [1]
+
+
+def test_dense_ranks_hand_instance(oracle_mod):
+    # column 0 holds {1, 0.5, 1, 0.25}: distinct ascending 0.25 < 0.5 < 1, so
+    # the ranks are 2, 1, 2, 0 and there are 3 distinct values; column 1
+    # holds {-0.0, +0.0, 2, 2}: -0.0 and +0.0 are one value (below 2), so the
+    # ranks are 0, 0, 1, 1 and there are 2
+    x = np.array([[1.0, -0.0], [0.5, 0.0], [1.0, 2.0], [0.25, 2.0]], np.float32)
+    ranks, distinct = oracle_mod.dense_ranks(x)
+    np.testing.assert_array_equal(ranks, [[2, 0], [1, 0], [2, 1], [0, 1]])
+    np.testing.assert_array_equal(distinct, [3, 2])
+    # no points: no distinct values
+    r0, d0 = oracle_mod.dense_ranks(np.zeros((0, 3), np.float32))
+    assert r0.shape == (0, 3)
+    np.testing.assert_array_equal(d0, [0, 0, 0])
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_dense_ranks_brute_force(oracle_mod, seed):
+    # rank = how many distinct values of the column lie below the value,
+    # counted with a Python set (which, like ==, takes -0.0 and +0.0 as one)
+    rng = np.random.default_rng(seed)
+    x = (rng.integers(-4, 5, size=(60, 4)) / 4).astype(np.float32)  # many ties, both zeros
+    x[rng.random(x.shape) < 0.1] *= np.float32(-1.0)
+    ranks, distinct = oracle_mod.dense_ranks(x)
+    for a in range(4):
+        vals = {float(v) for v in x[:, a]}
+        assert distinct[a] == len(vals)
+        for i in range(60):
+            assert ranks[i, a] == sum(1 for v in vals if v < float(x[i, a]))
+
+
+@pytest.mark.parametrize("kind,d", [("anticorrelated", 3), ("independent", 6), ("correlated", 8)])
+def test_dense_ranks_keep_the_skyline(oracle_mod, kind, d):
+    # Def. 1 compares attributes only by order, and the dense rank is strictly
+    # increasing in the value, so the skyline of the ranks is the skyline of
+    # the values; quantised inputs put ties into every column
+    x = getattr(datagen, kind)(3000, d, 40 + d)
+    for pts in (x, np.round(x * 16) / 16):
+        pts = pts.astype(np.float32)
+        ranks, distinct = oracle_mod.dense_ranks(pts)
+        assert (ranks.max(axis=0) + 1 == distinct).all()
+        np.testing.assert_array_equal(oracle_mod.skyline_indices(ranks.astype(np.float32)),
+                                      oracle_mod.skyline_indices(pts))
