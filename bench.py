@@ -460,21 +460,24 @@ def gpu_arm(args, rank, world, local):
     e2e_value = pts_per_step * k_e2e * world / e2e_s
 
     # roofline of the dominance kernel (k_engine): algorithmic compares
-    # (oracle test count x d) over its measured launch time, against three
+    # (oracle test count x d) over its measured launch time, against four
     # denominators: the derived FP32-compare peak (SMs x 64 compare lanes x
     # the maximum SM clock), the library's compare-rate probe (measured on
-    # this GPU), and the ceiling of the instruction the hot loop actually
-    # issues (sub.rn.f16x2 on the 128-lane FMA pipe: one attribute of two
-    # tests per lane per clock)
+    # this GPU), the nominal ceiling of the instruction the hot loop issues
+    # (sub.rn.f16x2 on 128 FMA lanes: one attribute of two tests per lane
+    # per clock), and the library's rejection-loop probe (the engine's own
+    # scan step run alone, measured on this GPU)
     wc = load_workcounts()
     roof = None
     dom_ms_per_step = acc["dom_ms"] / args.steps
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     clk_ghz = (clk.get("sm_max_mhz") or 2070.0) / 1e3
-    probe_tcmp = None
+    probe_tcmp = probe_reject = None
     try:
         rate, _ = ctx.probe_compare_rate()
         probe_tcmp = rate / 1e12
+        rate, _ = ctx.probe_reject_rate()
+        probe_reject = rate / 1e12
     except native.SkylineError:
         pass
     if wc:
@@ -494,9 +497,15 @@ def gpu_arm(args, rank, world, local):
                 "peak_probe": probe_tcmp, "frac_probe": achieved / probe_tcmp if probe_tcmp else None,
                 "f16x2_pipe_ceiling": f16, "frac_f16x2_pipe": achieved / f16,
                 "f16x2_source": f"{sms} SMs x 128 FMA lanes x 2 dim-compares per sub.rn.f16x2 x {clk_ghz:.3f} GHz",
+                "peak_reject_probe": probe_reject,
+                "frac_reject_probe": achieved / probe_reject if probe_reject else None,
+                "reject_probe_source": "sky_probe_reject_rate: the engine's f16x2 scan step alone, every test "
+                                       "failing, 4 CTAs x 128 threads per SM, measured",
                 "local": {"achieved": a_loc, "frac": a_loc / peak, "frac_f16x2_pipe": a_loc / f16,
+                          "frac_reject_probe": a_loc / probe_reject if probe_reject else None,
                           "ms": loc_ms, "algorithmic_tests": t_loc},
                 "merge": {"achieved": a_mer, "frac": a_mer / peak, "frac_f16x2_pipe": a_mer / f16,
+                          "frac_reject_probe": a_mer / probe_reject if probe_reject else None,
                           "ms": mer_ms, "algorithmic_tests": t_mer},
                 "traffic": engine_traffic(), "traffic_unit": "DRAM bytes per step (ncu, both engine launches)",
                 "algorithmic_tests_per_step": tests,

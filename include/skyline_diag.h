@@ -27,6 +27,20 @@ extern "C" {
 sky_status sky_probe_compare_rate(sky_ctx* ctx, uint32_t iterations, double* compares_per_s,
                                   uint32_t* sm_count);
 
+/* Runs the dominance engine's first test as a throughput loop on the
+   context's device and stream: 128-thread CTAs, four per SM (as the engine
+   runs), each lane holding four candidates' FP16 images (d = 6, duplicated
+   per word) and scanning a staged shared-memory block two dominator pairs
+   per step -- one f16x2 subtraction per attribute and candidate, the sign
+   words OR-ed per test and AND-ed per step, a branch on the result -- the
+   instruction sequence of the engine's scan when every test fails (a
+   confirmation), about `iterations` x 512 tests per thread.
+   *dim_compares_per_s receives the tests per second x 6 (the practical
+   ceiling of the engine's compare loop); *sm_count the SMs used.  Blocks
+   until done.  Errors: SKY_EINVAL (NULL outputs or iterations == 0),
+   SKY_ENOMEM, SKY_ECUDA. */
+sky_status sky_probe_reject_rate(sky_ctx* ctx, uint32_t iterations, double* dim_compares_per_s,
+                                 uint32_t* sm_count);
 /* Test hook of the engine's bounded waits (the paper has no counterpart; it
    exists so that a test can show that a device-side wait which never ends
    is turned into an error status without faulting or hanging the GPU).

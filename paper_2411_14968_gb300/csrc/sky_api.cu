@@ -328,6 +328,24 @@ sky_status sky_probe_compare_rate(sky_ctx* ctx, uint32_t iterations, double* com
   return SKY_OK;
 }
 
+sky_status sky_probe_reject_rate(sky_ctx* ctx, uint32_t iterations, double* dim_compares_per_s,
+                                 uint32_t* sm_count) {
+  if (!ctx || !dim_compares_per_s || !sm_count || iterations == 0) return SKY_EINVAL;
+  if (cudaSetDevice(ctx->run.device) != cudaSuccess) return SKY_ECUDA;
+  u32* sink = nullptr;
+  if (cudaMalloc(&sink, 256) != cudaSuccess) {
+    cudaGetLastError();
+    return SKY_ENOMEM;
+  }
+  cudaError_t e = probe_reject_rate(iterations, ctx->run.stream, dim_compares_per_s, sm_count, sink);
+  cudaFree(sink);
+  if (e != cudaSuccess) {
+    ctx->run.last_error = std::string("reject probe: ") + cudaGetErrorString(e);
+    return SKY_ECUDA;
+  }
+  return SKY_OK;
+}
+
 sky_status sky_diag_engine_wait_test(sky_ctx* ctx, uint64_t wait_limit_ns, uint32_t withhold_task) {
   if (!ctx || wait_limit_ns < 1000000ull) return SKY_EINVAL;
   ctx->run.test_wait_ns = wait_limit_ns;

@@ -359,5 +359,6 @@ int device_sm_count();
 
 // Compare-throughput probe (sky_probe.cu).
 cudaError_t probe_compare_rate(u32 iters, cudaStream_t st, double* per_s, u32* sms_out, u32* sink);
+cudaError_t probe_reject_rate(u32 iters, cudaStream_t st, double* per_s, u32* sms_out, u32* sink);
 
 }  // namespace sky

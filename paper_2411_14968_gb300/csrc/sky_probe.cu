@@ -106,7 +106,93 @@ __global__ void __launch_bounds__(256) k_probe_cmp(u32 iters, float seed, u32* s
   if (acc == 0xffffffffu) sink[0] = acc;  // keeps the loop live
 }
 
+// The engine's first test as a throughput loop: the scan step of a warp
+// whose 4 candidates per lane (d = 6, FP16 images duplicated per word) all
+// survive a staged block of dominator pairs -- per step 2 pairs from shared
+// memory (broadcast loads), one f16x2 subtraction per attribute and
+// candidate, the sign words OR-ed per test and AND-ed over the step, and
+// the step's branch on the result.  The staged images (32768) exceed every
+// candidate's (at most 1.0), so every test fails, as in a confirmation.
+constexpr int RJ_D = 6, RJ_R = 4, RJ_UP = 2, RJ_BLOCK = 1024;
+
+__device__ __forceinline__ u32 probe_hsub2(u32 t, u32 w) {
+  u32 r;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(t), "r"(w));
+  return r;
+}
+
+__global__ void __launch_bounds__(128) k_probe_reject(u32 iters, u32 seed, u32* sink) {
+  __shared__ uint4 sb[RJ_BLOCK * 2];
+  for (int i = threadIdx.x; i < RJ_BLOCK * 2; i += blockDim.x)
+    sb[i] = make_uint4(0x78007800u, 0x78007800u, 0x78007800u, 0x78007800u);
+  __syncthreads();
+  u32 t[RJ_R][RJ_D];
+#pragma unroll
+  for (int r = 0; r < RJ_R; ++r)
+#pragma unroll
+    for (int k = 0; k < RJ_D; ++k) t[r][k] = (seed * (threadIdx.x + 7u * r + 3u * k)) & 0x3c003c00u;
+  u32 passes = 0;
+  for (u32 it = 0; it < iters; ++it) {
+    for (int j = 0; j < RJ_BLOCK; j += 2 * RJ_UP) {
+      u32 w[RJ_UP][RJ_D];
+#pragma unroll
+      for (int q = 0; q < RJ_UP; ++q) {
+        const uint4 a = sb[j + 2 * q], b = sb[j + 2 * q + 1];
+        w[q][0] = a.x;
+        w[q][1] = a.y;
+        w[q][2] = a.z;
+        w[q][3] = a.w;
+        w[q][4] = b.x;
+        w[q][5] = b.y;
+      }
+      u32 acc = 0xffffffffu;
+#pragma unroll
+      for (int q = 0; q < RJ_UP; ++q)
+#pragma unroll
+        for (int r = 0; r < RJ_R; ++r) {
+          u32 x = probe_hsub2(t[r][0], w[q][0]);
+#pragma unroll
+          for (int k = 1; k < RJ_D; ++k) x |= probe_hsub2(t[r][k], w[q][k]);
+          acc &= x;
+        }
+      if ((acc & 0x80008000u) != 0x80008000u) ++passes;  // never taken
+    }
+  }
+  if (passes == 0xffffffffu) sink[0] = passes;  // keeps the loop live
+}
+
 }  // namespace
+
+cudaError_t probe_reject_rate(u32 iters, cudaStream_t st, double* per_s, u32* sms_out, u32* sink) {
+  int sms = device_sm_count();
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_probe_reject, 128, 0);
+  if (e != cudaSuccess) return e;
+  // four CTAs per SM, as the engine runs
+  if (per_sm > 4 || per_sm < 1) per_sm = 4;
+  unsigned grid = (unsigned)(sms * per_sm);
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  note_launch();
+  k_probe_reject<<<grid, 128, 0, st>>>(iters / 8 + 1, 0x9e3779b9u, sink);  // warm-up
+  cudaEventRecord(a, st);
+  note_launch();
+  k_probe_reject<<<grid, 128, 0, st>>>(iters, 0x9e3779b9u, sink);
+  cudaEventRecord(b, st);
+  e = cudaEventSynchronize(b);
+  float ms = 0;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess) return e;
+  // tests per thread per iteration: RJ_BLOCK / (2 RJ_UP) steps x RJ_UP pairs
+  // x 2 dominators x RJ_R candidates
+  const double tests = (double)iters * (RJ_BLOCK / (2 * RJ_UP)) * RJ_UP * 2 * RJ_R * (double)grid * 128.0;
+  *per_s = tests * RJ_D / (ms * 1e-3);
+  *sms_out = (u32)sms;
+  return cudaGetLastError();
+}
 
 cudaError_t probe_compare_rate(u32 iters, cudaStream_t st, double* per_s, u32* sms_out, u32* sink) {
   int sms = device_sm_count();

@@ -111,7 +111,7 @@ EXPORTS = ["sky_params_init", "sky_create", "sky_set_stream", "sky_set_timing", 
            "sky_probe_compare_rate", "sky_skyline_static", "sky_skyline_batch", "sky_serve_config_init", "sky_query_bytes",
            "sky_serve_start", "sky_submit", "sky_poll", "sky_wait", "sky_serve_stop", "sky_autotune", "sky_autotune_batch",
            "sky_graph_capture", "sky_graph_launch", "sky_graph_destroy", "sky_diag_engine_wait_test",
-           "sky_rank_space"]
+           "sky_rank_space", "sky_probe_reject_rate"]
 
 _lock = threading.Lock()
 _lib = None
@@ -160,6 +160,8 @@ def load(build_if_missing: bool = True):
         L.sky_destroy.restype = None
         L.sky_probe_compare_rate.argtypes = [P, u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32)]
         L.sky_probe_compare_rate.restype = i32
+        L.sky_probe_reject_rate.argtypes = [P, u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u32)]
+        L.sky_probe_reject_rate.restype = i32
         L.sky_skyline_batch.argtypes = [P, ctypes.POINTER(SkyQuery), u32]
         L.sky_skyline_batch.restype = i32
         L.sky_serve_config_init.argtypes = [ctypes.POINTER(SkyServeConfig)]
@@ -272,6 +274,14 @@ class Context:
         rate = ctypes.c_double(0)
         sms = ctypes.c_uint32(0)
         self._check(self._L.sky_probe_compare_rate(self._h, int(iterations), ctypes.byref(rate), ctypes.byref(sms)))
+        return rate.value, sms.value
+
+    def probe_reject_rate(self, iterations: int = 200):
+        """Measured dim-compares per second of the engine's f16x2 rejection
+        loop run alone (sky_probe_reject_rate; diagnostic)."""
+        rate = ctypes.c_double(0)
+        sms = ctypes.c_uint32(0)
+        self._check(self._L.sky_probe_reject_rate(self._h, int(iterations), ctypes.byref(rate), ctypes.byref(sms)))
         return rate.value, sms.value
 
     def engine_wait_test(self, wait_limit_ns: int, withhold_task: int):
