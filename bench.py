@@ -907,6 +907,20 @@ def ncu_case(which: str):
             torch.cuda.synchronize()
             print(f"ncu case noseq: |Sky| = {r.shape[0]}, {ctx.stats()['launches']} launches per call")
         return
+    if which == "rank":
+        # rank space of 4M anticorrelated points, d = 8 (128 MB of input):
+        # the rank kernels and the sorts of sky_rank_space, per column
+        x = datagen.anticorrelated(4_000_000, 8, 3)
+        xt = torch.from_numpy(x).cuda()
+        with native.Context(0) as ctx:
+            ctx.set_timing(True)
+            for _ in range(2):
+                r, dist, _ = ctx.rank_space(xt)
+            torch.cuda.synchronize()
+            st = ctx.stats()
+            print(f"ncu case rank: distinct {dist.cpu().tolist()}, {st['launches']} launches, "
+                  f"{st['ms_total']:.3f} ms per call")
+        return
     if which == "c3":
         # one 4M-point d = 8 quantised independent query, Grid m = 2 (256
         # cells): the workload where the memory-bound stages bound the query
@@ -948,11 +962,12 @@ def main():
     ap.add_argument("--experiment", choices=["rep-filtering", "sweeps", "configs", "shapes", "fp16", "value-range"],
                     default=None,
                     help="run one of the paper's experiments instead of the benchmark")
-    ap.add_argument("--ncu-case", choices=["small", "batch", "c3", "noseq"], default=None,
+    ap.add_argument("--ncu-case", choices=["small", "batch", "c3", "noseq", "rank"], default=None,
                     help="run a profiling case only, twice, default knobs, no timing: 'small' = one query "
                          "(anticorrelated N=200k, d=6, Sliced p=64); 'batch' = the benchmark's batched step; "
                          "'c3' = one quantised independent query, N=4M, d=8, Grid m=2; 'noseq' = one skewed "
-                         "query, N=200k, d=6, Angular (4,4,2,2,2) + Sorted reps, NoSeq")
+                         "query, N=200k, d=6, Angular (4,4,2,2,2) + Sorted reps, NoSeq; 'rank' = sky_rank_space "
+                         "of 4M anticorrelated points, d=8")
     # FP32 compare peak in T compares/s; 0 derives it from the device's SM
     # count x 64 compare lanes per SM per clock x the maximum SM clock seen
     ap.add_argument("--compare-peak-tcmp", type=float, default=0.0)

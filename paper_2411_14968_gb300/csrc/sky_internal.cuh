@@ -113,12 +113,14 @@ struct RankScratch {
   u8* flag;       // n
   u32* incl;      // n
   u32* scan_tmp;  // scan_tmp_words(n)
+  u32* cols;      // d x n: the ranks column by column
 };
-// Dense ranks of every column of X (N x d row-major, device): ranks[i*d + a]
-// (optional), codes[i*code_stride + a] = rank_code(rank, distinct[a])
-// (optional), distinct[a] (optional, device).  NaN sets ERR_NAN in *err.
+// Dense ranks of every column of X (N x d row-major, device) into s.cols and
+// distinct[a] (device, d words), then row-major: ranks[i*d + a] (optional),
+// codes[i*d + a] = rank_code(rank, distinct[a]) (optional), and the codes
+// packed eight halves per point (optional).  NaN sets ERR_NAN in *err.
 cudaError_t launch_rank_space(const float* X, u64 n, u32 d, const RankScratch& s, u32* ranks,
-                              unsigned short* codes, u32 code_stride, u32* distinct, u32* err, cudaStream_t st);
+                              unsigned short* codes, uint4* packed, u32* distinct, u32* err, cudaStream_t st);
 
 // ---------------------------------------------------------------- prep (sky_prep.cu)
 struct PrepArgs {

@@ -661,13 +661,15 @@ sky_status Runner::enqueue(BatchState& B) {
     if (pr.normalize || (pl.normalize && pl.rep == SKY_REP_REGION))
       CK(launch_colmax(w.X, n, D, b.words + W_COLMAX, err, st));
     // rank images (by original index) in the union's image buffer, which is
-    // free until the local phase ends; keys, values, mask and head are
-    // rewritten by the prep and the sorts below
+    // free until the local phase ends; the column ranks in the window's
+    // point array (d x n words fit its 16 x vec_of(d) bytes per point), the
+    // distinct counts in the merge's position array, both idle until the
+    // local phase; keys, values, mask and head are rewritten by the prep and
+    // the sorts below
     if (pl.images == SKY_IMAGES_RANKS) {
-      CK(cudaMemsetAsync(b.uhc, 0, n * sizeof(uint4), st));
-      RankScratch rs{{b.keys[0], b.keys[1]}, {b.vals[0], b.vals[1]}, b.hist, b.mask, b.head, b.scan_tmp};
-      CK(launch_rank_space(w.X, n, (u32)D, rs, nullptr, reinterpret_cast<unsigned short*>(b.uhc), 8, nullptr,
-                           err, st));
+      RankScratch rs{{b.keys[0], b.keys[1]}, {b.vals[0], b.vals[1]}, b.hist, b.mask, b.head, b.scan_tmp,
+                     reinterpret_cast<u32*>(b.win)};
+      CK(launch_rank_space(w.X, n, (u32)D, rs, nullptr, nullptr, b.uhc, b.mpos, err, st));
     }
     CK(launch_prep(pr, D, st));
     int sel = 0;

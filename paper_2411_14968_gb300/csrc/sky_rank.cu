@@ -51,19 +51,41 @@ __global__ void k_rank_heads(const u64* __restrict__ keys, u64 n, u8* __restrict
   flag[r] = (r == 0 || keys[r] != keys[r - 1]) ? 1 : 0;
 }
 
-// incl[r] - 1 is the dense rank of the value at sorted position r and
-// *distinct (the scan's total) the column's number of distinct values.
-__global__ void k_rank_scatter(const u32* __restrict__ sorted_idx, const u32* __restrict__ incl, u64 n, u32 d,
-                               u32 a, const u32* __restrict__ distinct, u32* __restrict__ ranks,
-                               unsigned short* __restrict__ codes, u32 code_stride, u32* __restrict__ distinct_out) {
+// incl[r] - 1 is the dense rank of the value at sorted position r; it goes
+// to the point's own index in the column's rank array (random 4-byte writes
+// into one n-word array, which stays in L2 for the columns of up to tens of
+// millions of points), and *total (the scan's total, the column's number of
+// distinct values) to distinct[a].
+__global__ void k_rank_scatter(const u32* __restrict__ sorted_idx, const u32* __restrict__ incl, u64 n,
+                               const u32* __restrict__ total, u32* __restrict__ col, u32* __restrict__ distinct,
+                               u32 a) {
   const u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
-  const u32 R = *distinct;
-  const u32 rank = incl[r] - 1;
-  const u64 i = sorted_idx[r];
-  if (ranks) ranks[i * d + a] = rank;
-  if (codes) codes[i * code_stride + a] = (unsigned short)rank_code(rank, R);
-  if (r == 0 && distinct_out) distinct_out[a] = R;
+  col[sorted_idx[r]] = incl[r] - 1;
+  if (r == 0) distinct[a] = *total;
+}
+
+// Row-major outputs from the column rank arrays (cols[a * n + i]), one
+// point per thread, coalesced on both sides: ranks[i*d + a] (optional), the
+// codes of the rank images -- codes[i*d + a] (optional), or packed as one
+// uint4 of eight halves per point with the halves past d zero (optional).
+__global__ void k_rank_pack(const u32* __restrict__ cols, u64 n, u32 d, const u32* __restrict__ distinct,
+                            u32* __restrict__ ranks, unsigned short* __restrict__ codes,
+                            uint4* __restrict__ packed) {
+  const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  u32 c[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    c[a] = 0;
+    if ((u32)a < d) {
+      const u32 rank = cols[(u64)a * n + i];
+      if (ranks) ranks[i * d + a] = rank;
+      c[a] = rank_code(rank, distinct[a]);
+      if (codes) codes[i * d + a] = (unsigned short)c[a];
+    }
+  }
+  if (packed) packed[i] = make_uint4(c[0] | c[1] << 16, c[2] | c[3] << 16, c[4] | c[5] << 16, c[6] | c[7] << 16);
 }
 
 // Bump allocator over the Runner's workspace (sizes rounded to 256 bytes).
@@ -82,7 +104,7 @@ struct Bump {
 }  // namespace
 
 cudaError_t launch_rank_space(const float* X, u64 n, u32 d, const RankScratch& s, u32* ranks,
-                              unsigned short* codes, u32 code_stride, u32* distinct, u32* err, cudaStream_t st) {
+                              unsigned short* codes, uint4* packed, u32* distinct, u32* err, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const u32* total = s.scan_tmp + scan_total_index(n);
   for (u32 a = 0; a < d; ++a) {
@@ -102,12 +124,13 @@ cudaError_t launch_rank_space(const float* X, u64 n, u32 d, const RankScratch& s
     e = scan_u8(s.flag, s.incl, n, false, s.scan_tmp, st);
     if (e != cudaSuccess) return e;
     note_launch();
-    k_rank_scatter<<<rgrid(n), RT, 0, st>>>(s.vals[sel], s.incl, n, d, a, total, ranks, codes, code_stride,
-                                             distinct);
+    k_rank_scatter<<<rgrid(n), RT, 0, st>>>(s.vals[sel], s.incl, n, total, s.cols + (u64)a * n, distinct, a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  note_launch();
+  k_rank_pack<<<rgrid(n), RT, 0, st>>>(s.cols, n, d, distinct, ranks, codes, packed);
+  return cudaGetLastError();
 }
 
 #define RCK(expr)                                                                              \
@@ -153,6 +176,7 @@ sky_status Runner::rank_space(const float* points, u64 n, u32 d, u32* out_ranks,
     s->flag = c.take<u8>(n);
     s->incl = c.take<u32>(n);
     s->scan_tmp = c.take<u32>(scan_tmp_words(n));
+    s->cols = c.take<u32>(L);
     *rk = ranks_host ? c.take<u32>(L) : out_ranks;
     *cd = codes_host ? c.take<unsigned short>(L) : out_codes;
     *dist = c.take<u32>(8);
@@ -173,7 +197,9 @@ sky_status Runner::rank_space(const float* points, u64 n, u32 d, u32* out_ranks,
   const u64 l0 = launch_counter();
   if (x_host) RCK(cudaMemcpyAsync(const_cast<float*>(X), points, L * sizeof(float), cudaMemcpyHostToDevice, stream));
   RCK(cudaMemsetAsync(err, 0, sizeof(u32), stream));
-  RCK(launch_rank_space(X, n, d, s, rk, cd, d, dist, err, stream));
+  if (timing) RCK(cudaEventRecord(ev_[0], stream));
+  RCK(launch_rank_space(X, n, d, s, rk, cd, nullptr, dist, err, stream));
+  if (timing) RCK(cudaEventRecord(ev_[1], stream));
   if (ranks_host) RCK(cudaMemcpyAsync(out_ranks, rk, L * sizeof(u32), cudaMemcpyDeviceToHost, stream));
   if (codes_host) RCK(cudaMemcpyAsync(out_codes, cd, L * sizeof(unsigned short), cudaMemcpyDeviceToHost, stream));
   if (out_distinct)
@@ -184,6 +210,11 @@ sky_status Runner::rank_space(const float* points, u64 n, u32 d, u32* out_ranks,
   stats.n = n;
   stats.d = d;
   stats.launches = launch_counter() - l0;
+  if (timing) {
+    float ms = 0;
+    RCK(cudaEventElapsedTime(&ms, ev_[0], ev_[1]));
+    stats.ms_total = ms;  // the kernels only (no host copies)
+  }
   const u32 e = pinned_[0];
   if (e & ERR_NAN) return fail(SKY_EINVAL, "input contains NaN");
   if (e & ERR_TIMEOUT) return fail(SKY_ETIMEOUT, "a device-side wait timed out");
