@@ -95,6 +95,10 @@ cudaError_t scan_u8(const u8* in, u32* out, u64 n, bool exclusive, u32* tmp, cud
 size_t radix_work_words(u64 n);
 cudaError_t radix_sort(u64* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32* work, cudaStream_t st,
                        int* out_sel, const u32* n_dev = nullptr, u32* err = nullptr);
+// The same for 32-bit keys (hi_bit <= 32): 16 instead of 24 bytes moved per
+// key and pass.
+cudaError_t radix_sort(u32* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32* work, cudaStream_t st,
+                       int* out_sel, const u32* n_dev = nullptr, u32* err = nullptr);
 
 // ---------------------------------------------------------------- rank space (sky_rank.cu)
 // Codes of the rank images: the finite non-negative FP16 bit patterns
@@ -107,7 +111,7 @@ __host__ __device__ inline u32 rank_code(u32 rank, u32 R) {
   return R <= RANK_CODES ? rank : (u32)(((u64)rank * (RANK_CODES - 1)) / (R - 1));
 }
 struct RankScratch {
-  u64* keys[2];   // n each
+  u64* keys[2];   // n each (the sort uses them as 32-bit key arrays)
   u32* vals[2];   // n each
   u32* work;      // radix_work_words(n)
   u8* flag;       // n

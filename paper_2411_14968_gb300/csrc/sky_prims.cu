@@ -221,8 +221,11 @@ __device__ __forceinline__ u64 sort_timer() {
   return t;
 }
 
-// Counts the digits of every pass over one tile per block.
-__global__ void k_sort_hist(const u64* __restrict__ k, u64 n, const u32* __restrict__ n_dev, int lo_bit,
+// Counts the digits of every pass over one tile per block.  K is the key
+// type (u64, or u32 for keys of at most 32 bits: a third less traffic per
+// pass).
+template <class K>
+__global__ void k_sort_hist(const K* __restrict__ k, u64 n, const u32* __restrict__ n_dev, int lo_bit,
                             int npass, int last_bits, u32* __restrict__ ghist) {
   __shared__ u32 h[MAX_PASS][RT];
   const int tid = threadIdx.x;
@@ -231,11 +234,11 @@ __global__ void k_sort_hist(const u64* __restrict__ k, u64 n, const u32* __restr
   n = radix_count(n, n_dev);
   const u64 base = (u64)blockIdx.x * RTILE;
   // the tile's keys are loaded together (one memory latency), then counted
-  u64 kr[RIPT];
+  K kr[RIPT];
 #pragma unroll
   for (int r = 0; r < RIPT; ++r) {
     const u64 e = base + (u64)r * RT + tid;
-    kr[r] = e < n ? k[e] : 0ull;
+    kr[r] = e < n ? k[e] : (K)0;
   }
 #pragma unroll
   for (int r = 0; r < RIPT; ++r) {
@@ -273,7 +276,8 @@ __global__ void k_sort_scan(u32* ghist, int npass) {
 constexpr int KPW = RIPT * 32;  // keys per warp of a tile
 constexpr int LBW = 8;          // predecessor status words read per look-back step
 
-__global__ void k_sort_pass(const u64* __restrict__ kin, const u32* __restrict__ vin, u64* __restrict__ kout,
+template <class K>
+__global__ void k_sort_pass(const K* __restrict__ kin, const u32* __restrict__ vin, K* __restrict__ kout,
                             u32* __restrict__ vout, u64 n, const u32* __restrict__ n_dev, int shift, u32 mask,
                             const u32* __restrict__ gofs, u64* status, u32* tile_ctr, u32 pass_tag, u32* err) {
   __shared__ u32 s_tile;
@@ -292,12 +296,12 @@ __global__ void k_sort_pass(const u64* __restrict__ kin, const u32* __restrict__
   const u64 wbase = base + (u64)warp * KPW;
   // the warp's keys and values are loaded together up front (one memory
   // latency for the tile instead of one per iteration of the passes below)
-  u64 kr[RIPT];
+  K kr[RIPT];
   u32 vr[RIPT];
 #pragma unroll
   for (int r = 0; r < RIPT; ++r) {
     const u64 e = wbase + (u64)r * 32 + lane;
-    kr[r] = e < n ? kin[e] : 0ull;
+    kr[r] = e < n ? kin[e] : (K)0;
   }
 #pragma unroll
   for (int r = 0; r < RIPT; ++r) {
@@ -380,7 +384,7 @@ __global__ void k_sort_pass(const u64* __restrict__ kin, const u32* __restrict__
   for (int r = 0; r < RIPT; ++r) {
     const u64 e = wbase + (u64)r * 32 + lane;
     const bool valid = e < n;
-    const u64 key = kr[r];
+    const K key = kr[r];
     const u32 val = vr[r];
     const u32 dg = valid ? (u32)(key >> shift) & mask : 0xffffffffu;
     const u32 peers = __match_any_sync(FULL, dg);
@@ -407,14 +411,15 @@ __global__ void k_sort_pass(const u64* __restrict__ kin, const u32* __restrict__
 constexpr u32 SMALL_SORT_MAX = 4096;
 constexpr size_t SMALL_DSMEM = (size_t)SMALL_SORT_MAX * (sizeof(u64) + sizeof(u32));
 
-__global__ void __launch_bounds__(RT) k_sort_small(u64* k0, u64* k1, u32* v0, u32* v1, u64 n,
+template <class K>
+__global__ void __launch_bounds__(RT) k_sort_small(K* k0, K* k1, u32* v0, u32* v1, u64 n,
                                                    const u32* __restrict__ n_dev, int lo_bit, int npass,
                                                    int last_bits) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ u32 s_w[RT / 32][RT];  // per-warp digit counts, then per-warp digit starts
   __shared__ u32 s_start[RT];       // start of each digit in the output
   __shared__ u32 s_sc[32];
-  u64* ks = reinterpret_cast<u64*>(s_dyn);
+  K* ks = reinterpret_cast<K*>(s_dyn);
   u32* vs = reinterpret_cast<u32*>(ks + SMALL_SORT_MAX);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const u32 lt = (1u << lane) - 1u;
@@ -424,9 +429,9 @@ __global__ void __launch_bounds__(RT) k_sort_small(u64* k0, u64* k1, u32* v0, u3
   const u32 wb = warp * per;
   for (int p = 0; p < npass; ++p) {
     // pass p reads buffer p % 2 and writes buffer (p + 1) % 2
-    const u64* kin = (p & 1) ? k1 : k0;
+    const K* kin = (p & 1) ? k1 : k0;
     const u32* vin = (p & 1) ? v1 : v0;
-    u64* kout = (p & 1) ? k0 : k1;
+    K* kout = (p & 1) ? k0 : k1;
     u32* vout = (p & 1) ? v0 : v1;
     for (u32 i = tid; i < m; i += RT) {
       ks[i] = kin[i];
@@ -459,7 +464,7 @@ __global__ void __launch_bounds__(RT) k_sort_small(u64* k0, u64* k1, u32* v0, u3
     for (u32 it = 0; it < per; it += 32) {
       const u32 e = wb + it + lane;
       const bool valid = e < m;
-      const u64 key = valid ? ks[e] : 0ull;
+      const K key = valid ? ks[e] : (K)0;
       const u32 dg = valid ? (u32)(key >> shift) & mask : 0xffffffffu;
       const u32 peers = __match_any_sync(FULL, dg);
       if (valid) {
@@ -496,20 +501,23 @@ size_t radix_work_words(u64 n) {
   return W_STATUS + 2 * (size_t)RT * (size_t)(nb ? nb : 1);
 }
 
-cudaError_t radix_sort(u64* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32* work, cudaStream_t st,
-                       int* out_sel, const u32* n_dev, u32* err) {
+namespace {
+
+template <class K>
+cudaError_t radix_sort_impl(K* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32* work, cudaStream_t st,
+                            int* out_sel, const u32* n_dev, u32* err) {
   *out_sel = 0;
   if (n <= 1 || hi_bit <= lo_bit) return cudaSuccess;
   const int bits = hi_bit - lo_bit;
   const int npass = (bits + 7) / 8;
-  if (npass > MAX_PASS || n >= (1ull << 32)) return cudaErrorInvalidValue;
+  if (npass > MAX_PASS || n >= (1ull << 32) || hi_bit > (int)(8 * sizeof(K))) return cudaErrorInvalidValue;
   const int last_bits = bits - 8 * (npass - 1);
   if (n <= SMALL_SORT_MAX) {
-    cudaError_t e = cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_sort_small<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)SMALL_DSMEM);
     if (e != cudaSuccess) return e;
     note_launch();
-    k_sort_small<<<1, RT, SMALL_DSMEM, st>>>(k[0], k[1], v[0], v[1], n, n_dev, lo_bit, npass, last_bits);
+    k_sort_small<K><<<1, RT, SMALL_DSMEM, st>>>(k[0], k[1], v[0], v[1], n, n_dev, lo_bit, npass, last_bits);
     *out_sel = npass & 1;  // the last pass wrote buffer npass % 2
     return cudaGetLastError();
   }
@@ -520,7 +528,7 @@ cudaError_t radix_sort(u64* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32*
   cudaError_t e = cudaMemsetAsync(work, 0, radix_work_words(n) * sizeof(u32), st);
   if (e != cudaSuccess) return e;
   note_launch();
-  k_sort_hist<<<(unsigned)nb, RT, 0, st>>>(k[0], n, n_dev, lo_bit, npass, last_bits, ghist);
+  k_sort_hist<K><<<(unsigned)nb, RT, 0, st>>>(k[0], n, n_dev, lo_bit, npass, last_bits, ghist);
   note_launch();
   k_sort_scan<<<1, RT, 0, st>>>(ghist, npass);
   int sel = 0;
@@ -528,12 +536,24 @@ cudaError_t radix_sort(u64* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32*
     const int shift = lo_bit + 8 * p;
     const u32 mask = p == npass - 1 ? (1u << last_bits) - 1u : 0xffu;
     note_launch();
-    k_sort_pass<<<(unsigned)nb, RT, 0, st>>>(k[sel], v[sel], k[sel ^ 1], v[sel ^ 1], n, n_dev, shift, mask,
-                                             ghist + (size_t)p * RT, status, ctr + p, (u32)(p + 1), err);
+    k_sort_pass<K><<<(unsigned)nb, RT, 0, st>>>(k[sel], v[sel], k[sel ^ 1], v[sel ^ 1], n, n_dev, shift, mask,
+                                                ghist + (size_t)p * RT, status, ctr + p, (u32)(p + 1), err);
     sel ^= 1;
   }
   *out_sel = sel;
   return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t radix_sort(u64* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32* work, cudaStream_t st,
+                       int* out_sel, const u32* n_dev, u32* err) {
+  return radix_sort_impl<u64>(k, v, n, lo_bit, hi_bit, work, st, out_sel, n_dev, err);
+}
+
+cudaError_t radix_sort(u32* k[2], u32* v[2], u64 n, int lo_bit, int hi_bit, u32* work, cudaStream_t st,
+                       int* out_sel, const u32* n_dev, u32* err) {
+  return radix_sort_impl<u32>(k, v, n, lo_bit, hi_bit, work, st, out_sel, n_dev, err);
 }
 
 }  // namespace sky

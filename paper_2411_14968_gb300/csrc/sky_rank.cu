@@ -31,7 +31,7 @@ inline unsigned rgrid(u64 n) { return (unsigned)((n + RT - 1) / RT); }
 
 // Sort keys of attribute a: fkey of the value (-0.0 read as +0.0), with the
 // point's index as the sort's value.  A NaN is flagged (and sorted as 0).
-__global__ void k_rank_keys(const float* __restrict__ X, u64 n, u32 d, u32 a, u64* __restrict__ keys,
+__global__ void k_rank_keys(const float* __restrict__ X, u64 n, u32 d, u32 a, u32* __restrict__ keys,
                             u32* __restrict__ vals, u32* err) {
   const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -45,7 +45,7 @@ __global__ void k_rank_keys(const float* __restrict__ X, u64 n, u32 d, u32 a, u6
 }
 
 // flag[r] = 1 where sorted position r starts a run of equal values.
-__global__ void k_rank_heads(const u64* __restrict__ keys, u64 n, u8* __restrict__ flag) {
+__global__ void k_rank_heads(const u32* __restrict__ keys, u64 n, u8* __restrict__ flag) {
   const u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   flag[r] = (r == 0 || keys[r] != keys[r - 1]) ? 1 : 0;
@@ -107,18 +107,19 @@ cudaError_t launch_rank_space(const float* X, u64 n, u32 d, const RankScratch& s
                               unsigned short* codes, uint4* packed, u32* distinct, u32* err, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const u32* total = s.scan_tmp + scan_total_index(n);
+  // 32-bit sort keys in the key buffers
+  u32* k2[2] = {reinterpret_cast<u32*>(s.keys[0]), reinterpret_cast<u32*>(s.keys[1])};
   for (u32 a = 0; a < d; ++a) {
     note_launch();
-    k_rank_keys<<<rgrid(n), RT, 0, st>>>(X, n, d, a, s.keys[0], s.vals[0], err);
+    k_rank_keys<<<rgrid(n), RT, 0, st>>>(X, n, d, a, k2[0], s.vals[0], err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    u64* k2[2] = {s.keys[0], s.keys[1]};
     u32* v2[2] = {s.vals[0], s.vals[1]};
     int sel = 0;
     e = radix_sort(k2, v2, n, 0, 32, s.work, st, &sel, nullptr, err);
     if (e != cudaSuccess) return e;
     note_launch();
-    k_rank_heads<<<rgrid(n), RT, 0, st>>>(s.keys[sel], n, s.flag);
+    k_rank_heads<<<rgrid(n), RT, 0, st>>>(k2[sel], n, s.flag);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = scan_u8(s.flag, s.incl, n, false, s.scan_tmp, st);
