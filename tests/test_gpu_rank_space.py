@@ -152,3 +152,47 @@ def test_rank_images_in_a_batch(ctx, oracle_mod, torch_cuda):
     got = ctx.skyline_batch([(torch.from_numpy(x).cuda(), p) for x, p in zip(xs, ps)])
     for x, g in zip(xs, got):
         np.testing.assert_array_equal(g.cpu().numpy().astype(np.uint32), oracle_mod.skyline_indices(x))
+
+
+def test_rank_images_graph_serving_autotune(ctx, oracle_mod, torch_cuda):
+    """Rank images through the other entry points: a captured batch replayed
+    (also after its inputs are rewritten in place), the serving loop, and the
+    autotuner, each checked against the oracle."""
+    from paper_2411_14968_gb300 import native
+    torch = torch_cuda
+    O = oracle_mod
+    off = np.float32(1024.0)
+    x0 = [datagen.anticorrelated(30000, 5, 90) + off, datagen.independent(8000, 4, 91) * np.float32(2.0 ** 17)]
+    x1 = [datagen.anticorrelated(30000, 5, 92) + off, datagen.independent(8000, 4, 93) * np.float32(2.0 ** 17)]
+    x0 = [np.ascontiguousarray(x, dtype=np.float32) for x in x0]
+    x1 = [np.ascontiguousarray(x, dtype=np.float32) for x in x1]
+    ps = [native.make_params(scheme="sliced", p=8, rep="sorted", images="ranks"),
+          native.make_params(scheme="grid", slices=[3] * 4, normalize=True, images="ranks")]
+    ops = [dict(scheme=O.SLICED, p=8, rep=O.REP_SORTED), dict(scheme=O.GRID, slices=[3] * 4, normalize=True)]
+    want0 = [O.partitioned(x, **kw)["indices"] for x, kw in zip(x0, ops)]
+    want1 = [O.partitioned(x, **kw)["indices"] for x, kw in zip(x1, ops)]
+    xt = [torch.from_numpy(x).cuda() for x in x0]
+    g = ctx.capture(list(zip(xt, ps)))
+    res, _ = g.run()
+    for r, w in zip(res, want0):
+        np.testing.assert_array_equal(r.cpu().numpy().astype(np.uint32), w)
+    for t, x in zip(xt, x1):
+        t.copy_(torch.from_numpy(x))
+    res, _ = g.run()
+    for r, w in zip(res, want1):
+        np.testing.assert_array_equal(r.cpu().numpy().astype(np.uint32), w)
+    g.close()
+    # serving: rank-image and value-image queries in flight together
+    ctx.serve_start(workers=2, max_batch=8)
+    try:
+        tickets = [(ctx.submit(x, p), w) for x, p, w in zip(x0 + x1, ps + ps, want0 + want1)]
+        tickets.append((ctx.submit(x0[0], native.make_params(scheme="sliced", p=8, rep="sorted")), want0[0]))
+        for t, w in tickets:
+            got, _ = ctx.wait(t)
+            np.testing.assert_array_equal(got, w)
+    finally:
+        ctx.serve_stop()
+    # the autotuner keeps the method parameters (rank images included)
+    tuned, ms = ctx.autotune(x0[0], params=ps[0], max_trials=6)
+    assert ms > 0 and tuned.images == native.IMAGES["ranks"]
+    np.testing.assert_array_equal(ctx.skyline(x0[0], params=tuned), want0[0])
