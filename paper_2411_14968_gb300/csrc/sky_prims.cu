@@ -215,6 +215,20 @@ __device__ __forceinline__ u64 radix_count(u64 n, const u32* n_dev) {
   return m < n ? m : n;
 }
 
+// The lanes of the warp holding the same digit as this lane (8-bit digits;
+// invalid lanes, dg = ~0, are nobody's peers): one ballot per digit bit,
+// so the cost does not depend on how many distinct digits the warp holds.
+__device__ __forceinline__ u32 digit_peers(u32 dg, bool valid) {
+  u32 peers = __ballot_sync(FULL, valid);
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const bool bit = (dg >> b) & 1u;
+    const u32 bal = __ballot_sync(FULL, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
 __device__ __forceinline__ u64 sort_timer() {
   u64 t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -276,8 +290,10 @@ __global__ void k_sort_scan(u32* ghist, int npass) {
 constexpr int KPW = RIPT * 32;  // keys per warp of a tile
 constexpr int LBW = 8;          // predecessor status words read per look-back step
 
+// (Two blocks per SM, as the kernel ran before the ballots: unbounded, the
+// unrolled ballots of the 16 keys per thread take 254 registers.)
 template <class K>
-__global__ void k_sort_pass(const K* __restrict__ kin, const u32* __restrict__ vin, K* __restrict__ kout,
+__global__ void __launch_bounds__(RT, 2) k_sort_pass(const K* __restrict__ kin, const u32* __restrict__ vin, K* __restrict__ kout,
                             u32* __restrict__ vout, u64 n, const u32* __restrict__ n_dev, int shift, u32 mask,
                             const u32* __restrict__ gofs, u64* status, u32* tile_ctr, u32 pass_tag, u32* err) {
   __shared__ u32 s_tile;
@@ -315,7 +331,7 @@ __global__ void k_sort_pass(const K* __restrict__ kin, const u32* __restrict__ v
     const u64 e = wbase + (u64)r * 32 + lane;
     const bool valid = e < n;
     const u32 dg = valid ? (u32)(kr[r] >> shift) & mask : 0xffffffffu;
-    const u32 peers = __match_any_sync(FULL, dg);
+    const u32 peers = digit_peers(dg, valid);
     if (valid && lane == __ffs(peers) - 1) s_w[warp][dg] += __popc(peers);
     __syncwarp();
   }
@@ -387,7 +403,7 @@ __global__ void k_sort_pass(const K* __restrict__ kin, const u32* __restrict__ v
     const K key = kr[r];
     const u32 val = vr[r];
     const u32 dg = valid ? (u32)(key >> shift) & mask : 0xffffffffu;
-    const u32 peers = __match_any_sync(FULL, dg);
+    const u32 peers = digit_peers(dg, valid);
     u32 pos = 0;
     if (valid) pos = s_base[dg] + s_w[warp][dg] + __popc(peers & lt);
     __syncwarp();
@@ -446,7 +462,7 @@ __global__ void __launch_bounds__(RT) k_sort_small(K* k0, K* k1, u32* v0, u32* v
       const u32 e = wb + it + lane;
       const bool valid = e < m;
       const u32 dg = valid ? (u32)(ks[e] >> shift) & mask : 0xffffffffu;
-      const u32 peers = __match_any_sync(FULL, dg);
+      const u32 peers = digit_peers(dg, valid);
       if (valid && lane == __ffs(peers) - 1) s_w[warp][dg] += __popc(peers);
       __syncwarp();
     }
@@ -466,7 +482,7 @@ __global__ void __launch_bounds__(RT) k_sort_small(K* k0, K* k1, u32* v0, u32* v
       const bool valid = e < m;
       const K key = valid ? ks[e] : (K)0;
       const u32 dg = valid ? (u32)(key >> shift) & mask : 0xffffffffu;
-      const u32 peers = __match_any_sync(FULL, dg);
+      const u32 peers = digit_peers(dg, valid);
       if (valid) {
         const u32 pos = s_start[dg] + s_w[warp][dg] + __popc(peers & lt);
         kout[pos] = key;
