@@ -507,6 +507,16 @@ def gpu_arm(args, rank, world, local):
                 "merge": {"achieved": a_mer, "frac": a_mer / peak, "frac_f16x2_pipe": a_mer / f16,
                           "frac_reject_probe": a_mer / probe_reject if probe_reject else None,
                           "ms": mer_ms, "algorithmic_tests": t_mer},
+                "engine_tests": {
+                    "fp16": statistics.mean(st["tests_fp16"] for st in acc["stats"]),
+                    "fp16_per_algorithmic_test": statistics.mean(st["tests_fp16"] for st in acc["stats"]) / tests,
+                    "fp16_local": statistics.mean(st["tests_fp16_local"] for st in acc["stats"]),
+                    "fp16_local_per_algorithmic_test":
+                        statistics.mean(st["tests_fp16_local"] for st in acc["stats"]) / t_loc,
+                    "fp16_merge_per_algorithmic_test":
+                        statistics.mean(st["tests_fp16"] - st["tests_fp16_local"] for st in acc["stats"]) / t_mer,
+                    "unit": "tests per step counted by the engine (candidate slots x staged dominators of its "
+                            "16-bit test, dead slots included)"},
                 "traffic": engine_traffic(), "traffic_unit": "DRAM bytes per step (ncu, both engine launches)",
                 "algorithmic_tests_per_step": tests,
                 "kernel_ms_per_step": dom_ms_per_step,

@@ -134,6 +134,10 @@ typedef struct {
   uint64_t launches;           /* CUDA kernels the call launched */
   double ms_dom_local;         /* device time of the local-skyline dominance launches (timing on) */
   double ms_dom_merge;         /* device time of the final-phase dominance launch (timing on) */
+  uint64_t tests_fp16;         /* dominance tests of the engine's launches (local phase and sequential
+                                  merge; not NoSeq's): candidate slots x staged dominators its 16-bit
+                                  image test covered, slots of candidates already dead included */
+  uint64_t tests_fp16_local;   /* the part of tests_fp16 made by the local phase */
 } sky_stats;
 
 typedef struct sky_ctx sky_ctx;

@@ -460,7 +460,13 @@ __global__ void k_build_one_seg(SegArrays a, const u32* n_dev, int d, SegDesc* s
   *seg = sd;
 }
 
-__global__ void k_fold_max(const u32* src, u32* dst) { atomicMax(dst, *src); }
+// After an engine launch: its round count into the query's maximum, its
+// test count into the query's sum.
+__global__ void k_fold_engine(const u32* ctl, u32 round_word, u32 tests_word, u32* round_dst,
+                              unsigned long long* tests_dst) {
+  atomicMax(round_dst, ctl[round_word]);
+  atomicAdd(tests_dst, *reinterpret_cast<const unsigned long long*>(ctl + tests_word));
+}
 
 int g_sm_count = 0;
 
@@ -480,9 +486,9 @@ cudaError_t launch_build_one_seg(const SegArrays& a, const u32* n_dev, int d, Se
   return cudaGetLastError();
 }
 
-cudaError_t launch_fold_max(const u32* src, u32* dst, cudaStream_t st) {
+cudaError_t launch_fold_engine(const u32* ctl, u32* round_dst, unsigned long long* tests_dst, cudaStream_t st) {
   note_launch();
-  k_fold_max<<<1, 1, 0, st>>>(src, dst);
+  k_fold_engine<<<1, 1, 0, st>>>(ctl, engine_max_round_word(), engine_tests_word(), round_dst, tests_dst);
   return cudaGetLastError();
 }
 

@@ -110,7 +110,8 @@ constexpr u64 WAIT_NS = 4000000000ull;  // default bound of every wait (without 
 
 // Control words of a launch (zeroed by the host before it).  The queue word
 // is 64-bit: (tasks published << 32) | tickets reserved.
-enum { C_TICKET = 0, C_QUEUE = 2, C_LIVE = 4, C_FINISHED = 5, C_ABORT = 6, C_MAXROUND = 7, C_PROGRESS = 8 };
+enum { C_TICKET = 0, C_QUEUE = 2, C_LIVE = 4, C_FINISHED = 5, C_ABORT = 6, C_MAXROUND = 7, C_PROGRESS = 8,
+       C_TESTS = 10 /* u64: the launch's FP16 tests */ };
 
 __device__ __forceinline__ u64 globaltimer() {
   u64 t;
@@ -349,6 +350,18 @@ __device__ __forceinline__ void compact(const CandsT<D, RA>& a, CandsT<D, RB>& b
   __syncwarp();
 }
 
+// Dominance tests of a CTA (shared memory), added to the launch's total
+// when the CTA leaves: candidate slots x dominators the FP16 test covered
+// (dead slots included).  Counted per scan call, outside the scan loop.
+struct EngineCounts {
+  unsigned long long n16;
+};
+
+__device__ __forceinline__ void count_fp16(EngineCounts* k, u32 j0, u32 j1, u32 cnt, u32 slots) {
+  const u32 e = j1 < cnt ? j1 : cnt;
+  if ((threadIdx.x & 31) == 0 && e > j0) atomicAdd(&k->n16, (unsigned long long)(e - j0) * 32ull * slots);
+}
+
 // Scans the staged block sb[j..cnt) (dominator pairs, see put_pair_entry) for
 // the warp's candidates, RR slots per lane.  Every 32 dominators the warp
 // counts its live candidates; it stops early when none is left or when they
@@ -439,13 +452,14 @@ __device__ __forceinline__ u32 scan_steps(const uint4* sb, u32 j, u32 cnt, const
 template <int D>
 __device__ __forceinline__ void scan_smem(const uint4* sb, u32 cnt, const DomSrc& src, const float4* pts,
                                           CandsT<D, R>& c,
-                                          uint4* sc, u32* sp, u8* alive) {
+                                          uint4* sc, u32* sp, u8* alive, EngineCounts* k) {
   u32 n = alive_count(c);
   u32 j = 0;
   if constexpr (R == 2) {
     // 2 slots per lane, then 1
     if (n > 32) {
       j = scan_steps<D, 2>(sb, 0, cnt, src, pts, c, &n);
+      count_fp16(k, 0, j, cnt, 2);
       if (j >= cnt || n == 0) {
         write_kills(c, alive);
         return;
@@ -454,12 +468,13 @@ __device__ __forceinline__ void scan_smem(const uint4* sb, u32 cnt, const DomSrc
     CandsT<D, 1> c1;
     compact(c, c1, sc, sp, alive);
     if (n == 0) return;
-    scan_steps<D, 1>(sb, j, cnt, src, pts, c1, &n);
+    count_fp16(k, j, scan_steps<D, 1>(sb, j, cnt, src, pts, c1, &n), cnt, 1);
     write_kills(c1, alive);
   } else {
     // 4 slots per lane, then 2, then 1
     if (n > 64) {
       j = scan_steps<D, 4>(sb, 0, cnt, src, pts, c, &n);
+      count_fp16(k, 0, j, cnt, 4);
       if (j >= cnt || n == 0) {
         write_kills(c, alive);
         return;
@@ -469,7 +484,9 @@ __device__ __forceinline__ void scan_smem(const uint4* sb, u32 cnt, const DomSrc
     if (n > 32) {
       CandsT<D, 2> c2;
       compact(c, c2, sc, sp, alive);
-      j = scan_steps<D, 2>(sb, j, cnt, src, pts, c2, &n);
+      const u32 j2 = scan_steps<D, 2>(sb, j, cnt, src, pts, c2, &n);
+      count_fp16(k, j, j2, cnt, 2);
+      j = j2;
       if (j >= cnt || n == 0) {
         write_kills(c2, alive);
         return;
@@ -479,7 +496,7 @@ __device__ __forceinline__ void scan_smem(const uint4* sb, u32 cnt, const DomSrc
       compact(c, c1, sc, sp, alive);
       if (n == 0) return;
     }
-    scan_steps<D, 1>(sb, j, cnt, src, pts, c1, &n);
+    count_fp16(k, j, scan_steps<D, 1>(sb, j, cnt, src, pts, c1, &n), cnt, 1);
     write_kills(c1, alive);
   }
 }
@@ -696,6 +713,7 @@ struct Shared {
   uint4* pbuf;  // and its buffer
   u32 abort_seen;  // the launch's abort flag was seen set
   u32 pcopies[2];  // bulk copies issued into each buffer (by its producers, one at a time)
+  EngineCounts counts;
 };
 
 // Tile status words of the ordered compaction (decoupled look-back): the
@@ -918,7 +936,7 @@ __device__ void item_a(const Params& P, const SegDesc& sd, const Meta& mt, const
     }
     if (__any_sync(FULL, any_alive(c))) {
       DomSrc src{sd.win, nullptr, 0};
-      scan_smem<D>(staged, cnt, src, sd.pts, c, S.scode[warp], S.spos[warp], sd.alive);
+      scan_smem<D>(staged, cnt, src, sd.pts, c, S.scode[warp], S.spos[warp], sd.alive, &S.counts);
     }
   }
   // the staged buffer is refilled by a bulk copy once every warp is past
@@ -1116,7 +1134,7 @@ __device__ void item_b(const Params& P, const SegDesc& sd, const Meta& mt, const
       load_cand<D>(sd, pos, valid, c, r);
     }
     if (__any_sync(FULL, any_alive(c))) {
-      scan_smem<D>(staged, cnt, src, sd.pts, c, S.scode[warp], S.spos[warp], sd.alive);
+      scan_smem<D>(staged, cnt, src, sd.pts, c, S.scode[warp], S.spos[warp], sd.alive, &S.counts);
     }
   }
   fence_proxy_async_smem();  // as in item_a
@@ -1272,6 +1290,7 @@ __global__ void __launch_bounds__(THREADS, 16 / WARPS) k_engine(Params P) {
     S.meta[0].state = M_EMPTY;
     S.meta[1].state = M_EMPTY;
     S.abort_seen = 0;
+    S.counts.n16 = 0;
     S.pcopies[0] = S.pcopies[1] = 0;
   }
   __syncthreads();
@@ -1341,6 +1360,13 @@ __global__ void __launch_bounds__(THREADS, 16 / WARPS) k_engine(Params P) {
       break;
     }
   }
+  // the CTA's test counts into the launch's (every warp is past its last
+  // scan when the loop ends normally; after an abort the counts are partial)
+  if (threadIdx.x == 0) {
+    unsigned long long* tot = reinterpret_cast<unsigned long long*>(P.ctl + C_TESTS);
+    const unsigned long long a = atomicExch(&S.counts.n16, 0ull);
+    if (a) atomicAdd(tot, a);
+  }
 }
 
 
@@ -1395,6 +1421,7 @@ cudaError_t engine_run_variant<WARPS, R>(const SegDesc* segs_dev, u32 nseg, cons
 #if SKY_ENGINE_WARPS == 4 && SKY_ENGINE_R == 4
 // Facts of the engine that every shape shares.
 u32 engine_max_round_word() { return C_MAXROUND; }
+u32 engine_tests_word() { return C_TESTS; }
 u32 engine_max_dom_block() { return DBMAX; }
 size_t engine_task_bytes() { return sizeof(Task); }
 #endif

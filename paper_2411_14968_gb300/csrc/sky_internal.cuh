@@ -304,6 +304,7 @@ u64 engine_task_capacity(u64 total_points, u32 nseg, u32 chunk_min);
 size_t engine_task_bytes();
 // Control word that receives the largest round count of a launch.
 u32 engine_max_round_word();
+u32 engine_tests_word();  // the u64 control word counting the launch's FP16 dominance tests
 // Largest dominator block (points) the engine stages in shared memory.
 u32 engine_max_dom_block();
 
@@ -335,7 +336,9 @@ struct SegArrays {
 cudaError_t launch_build_segs(const u32* seg_off, u32 P, const u8* dropped, const SegArrays& a, int d,
                               SegDesc* segs, u32* nonempty, cudaStream_t st);
 cudaError_t launch_build_one_seg(const SegArrays& a, const u32* n_dev, int d, SegDesc* seg, cudaStream_t st);
-cudaError_t launch_fold_max(const u32* src, u32* dst, cudaStream_t st);
+// After an engine launch (whose control words are ctl): the launch's round
+// count into *round_dst (maximum) and its test count into *tests_dst (sum).
+cudaError_t launch_fold_engine(const u32* ctl, u32* round_dst, unsigned long long* tests_dst, cudaStream_t st);
 
 // Relative skyline (Section 4.2 definition): kill every alive candidate of
 // cand[0..nc) dominated by one of dom[0..nd) (nd = *nd_dev if given, else

@@ -121,7 +121,8 @@ constexpr u32 ORDERED_MAX_SEGS = 8;
 
 // word slots of Bufs::words
 enum { W_ERR = 0, W_COLMAX = 1, W_GRID_DROPPED = 9, W_KEPT = 10, W_NU = 11, W_SKY = 12, W_MAXROUND_LOCAL = 13,
-       W_MAXROUND_MERGE = 14, W_NONEMPTY = 15, W_HIST = 16, W_NOSEQ_CTR = 24, W_WORDS = 32 };
+       W_MAXROUND_MERGE = 14, W_NONEMPTY = 15, W_HIST = 16, W_NOSEQ_CTR = 24,
+       W_TESTS_LOCAL = 26, W_TESTS_MERGE = 28 /* u64 each: the engine's FP16 tests */, W_WORDS = 32 };
 
 size_t layout(const Plan& pl, u32 ang_words, Carve& c, Bufs* b) {
   const size_t start = c.off;
@@ -761,9 +762,11 @@ sky_status Runner::enqueue(BatchState& B) {
   ew.tasks = bb.tasks;
   ew.task_cap = bb.task_cap;
   ew.ctl = bb.ctl;
-  const u32* maxround = bb.ctl + engine_max_round_word();
-  auto engine = [&](const SegDesc* segs, u32 nseg, EngineCfg cfg, u32* err, u32* round_dst,
+  // the error word, round count and test counts of a launch go to one
+  // query's words (err = words + W_ERR)
+  auto engine = [&](const SegDesc* segs, u32 nseg, EngineCfg cfg, u32* err, u32* round_dst, u32 tests_word,
                     u32 ordered) -> cudaError_t {
+    unsigned long long* tests_dst = reinterpret_cast<unsigned long long*>(err - W_ERR + tests_word);
     cfg.ordered = ordered;
     cfg.wait_ns = test_wait_ns;
     cfg.withhold_task = test_withhold_task;
@@ -779,7 +782,7 @@ sky_status Runner::enqueue(BatchState& B) {
     } else {
       e = engine_run(segs, nseg, cfg, ew, err, st);
     }
-    if (e == cudaSuccess) e = launch_fold_max(maxround, round_dst, st);
+    if (e == cudaSuccess) e = launch_fold_engine(bb.ctl, round_dst, tests_dst, st);
     return e;
   };
   // the error word and round counter of a shared launch go to the first
@@ -797,14 +800,14 @@ sky_status Runner::enqueue(BatchState& B) {
     // the engine's chunk policy of a shared launch is the first query's
     // a local phase with few segments has large chunks, like the merge
     CK(engine(bb.segs, persistent_segs, first_persistent->pl.cfg, first_persistent->b.words + W_ERR,
-              first_persistent->b.words + W_MAXROUND_LOCAL,
+              first_persistent->b.words + W_MAXROUND_LOCAL, W_TESTS_LOCAL,
               persistent_segs <= ORDERED_MAX_SEGS ? ORD_LOOKBACK : ORD_LAST));
   }
   for (auto& w : ws) {
     if (w.q->n == 0 || w.pl.exec != SKY_EXEC_PLAIN) continue;
     for (u32 p = 0; p < w.pl.P; ++p)
       CK(engine(bb.segs + w.seg_base + p, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_LOCAL,
-                ORD_LOOKBACK));
+                W_TESTS_LOCAL, ORD_LOOKBACK));
   }
   record(9, B);
   CK(fork());
@@ -874,11 +877,11 @@ sky_status Runner::enqueue(BatchState& B) {
       }
     if (first)
       CK(engine(bb.msegs, cnt, first->pl.cfg, first->b.words + W_ERR, first->b.words + W_MAXROUND_MERGE,
-                ORD_LOOKBACK));
+                W_TESTS_MERGE, ORD_LOOKBACK));
     for (auto& w : ws)
       if (w.mseg >= 0 && w.pl.exec == SKY_EXEC_PLAIN)
         CK(engine(bb.msegs + w.mseg, 1, w.pl.cfg, w.b.words + W_ERR, w.b.words + W_MAXROUND_MERGE,
-                  ORD_LOOKBACK));
+                  W_TESTS_MERGE, ORD_LOOKBACK));
   }
   record(11, B);
   CK(fork());
@@ -931,10 +934,24 @@ sky_status Runner::finish(BatchState& B) {
   // the error word and round counts of a shared engine launch were written
   // to its first query: every query of the launch shares them
   u32 shared_err = 0, shared_round_local = 0, shared_round_merge = 0;
+  // dominance tests of the engine launches: every launch's went to one
+  // query's words; a query of the shared launches reports theirs, a query
+  // with launches of its own reports those, the batch reports all of them
+  // k: 0 local, 1 merge
+  u64 tests_all[2] = {0, 0}, tests_shared[2] = {0, 0};
+  auto tests_of = [](const Work& w, int k) {
+    u64 v;
+    memcpy(&v, &w.words[k == 0 ? W_TESTS_LOCAL : W_TESTS_MERGE], sizeof(v));
+    return v;
+  };
   for (u32 i = 0; i < nq; ++i) {
     Work& w = ws[i];
     if (w.q->n == 0) continue;
     memcpy(w.words, pinned_ + (size_t)i * W_WORDS, sizeof(w.words));
+    for (int k = 0; k < 2; ++k) {
+      tests_all[k] += tests_of(w, k);
+      if (w.pl.exec != SKY_EXEC_PLAIN) tests_shared[k] += tests_of(w, k);
+    }
     if (&w == first_persistent) {
       shared_err = w.words[W_ERR] & (ERR_TIMEOUT | ERR_CAPACITY);
       shared_round_local = w.words[W_MAXROUND_LOCAL];
@@ -996,6 +1013,10 @@ sky_status Runner::finish(BatchState& B) {
     S.rep_dropped = w.words[W_HIST + ST_REP];
     S.local_union = (u64)w.words[W_HIST + ST_MERGE] + w.words[W_HIST + ST_SKY];
     S.skyline = cnt;
+    u64 t[2];
+    for (int k = 0; k < 2; ++k) t[k] = shared ? tests_shared[k] : tests_of(w, k);
+    S.tests_fp16 = t[0] + t[1];
+    S.tests_fp16_local = t[0];
   }
   record(7, B);
   CK(cudaStreamSynchronize(st));
@@ -1014,6 +1035,8 @@ sky_status Runner::finish(BatchState& B) {
     stats.local_union += S.local_union;
     stats.skyline += S.skyline;
   }
+  stats.tests_fp16 = tests_all[0] + tests_all[1];
+  stats.tests_fp16_local = tests_all[0];
   stats.launches = B.graph ? B.kernels : launch_counter() - B.launches0;
   if (timing && !B.graph) {
     float ms = 0;

@@ -98,6 +98,8 @@ class SkyStats(ctypes.Structure):
         ("launches", ctypes.c_uint64),
         ("ms_dom_local", ctypes.c_double),
         ("ms_dom_merge", ctypes.c_double),
+        ("tests_fp16", ctypes.c_uint64),
+        ("tests_fp16_local", ctypes.c_uint64),
     ]
 
     def as_dict(self):

@@ -242,3 +242,33 @@ def test_local_dense_list_modes(ctx, oracle_mod):
     _check(ctx, oracle_mod, x, "sliced", p=12)
     _check(ctx, oracle_mod, x, "random", p=10, seed=4, rep="sorted")
     _check(ctx, oracle_mod, x, "sliced", p=12, chunk_min=4096, chunk_alpha_x4=64)
+
+
+def test_engine_test_counts(ctx, oracle_mod):
+    """sky_stats counts the engine's dominance tests: every point the engine
+    removed (stage 4, and stage 5 under the sequential merge) took at least
+    one, the local phase's are part of the total, and with NoSeq (no merge
+    in the engine) they are all of it."""
+    from paper_2411_14968_gb300 import native
+    x = datagen.anticorrelated(20000, 4, 5)
+    for merge in ("sequential", "noseq"):
+        for ex in ("persistent", "plain"):
+            _, _, stage = ctx.skyline(x, scheme="sliced", p=8, merge=merge, exec=ex, with_diag=True)
+            st = ctx.stats()
+            kills = int((stage == native.STAGE_LOCAL).sum())
+            if merge == "sequential":
+                kills += int((stage == native.STAGE_MERGE).sum())
+            assert st["tests_fp16"] >= kills > 0, (merge, ex, st["tests_fp16"], kills)
+            assert 0 < st["tests_fp16_local"] <= st["tests_fp16"]
+            if merge == "noseq":
+                assert st["tests_fp16_local"] == st["tests_fp16"]
+            else:
+                assert st["tests_fp16_local"] < st["tests_fp16"]
+    # a batch reports the tests of all its launches; a query of the shared
+    # launches reports theirs
+    ps = [native.make_params(scheme="sliced", p=8), native.make_params(scheme="grid", slices=[2] * 4)]
+    ctx.skyline_batch([(x, p) for p in ps])
+    st = ctx.stats()
+    ctx.skyline(x, params=ps[0])
+    alone = ctx.stats()
+    assert st["tests_fp16"] > alone["tests_fp16"] > 0
