@@ -325,13 +325,20 @@ __global__ void __launch_bounds__(RT, 2) k_sort_pass(const K* __restrict__ kin, 
     vr[r] = e < n ? vin[e] : 0u;
   }
   // this warp's digit counts (a digit's leader lane adds its peers; leaders
-  // of one iteration hold distinct digits, so no atomics are needed)
+  // of one iteration hold distinct digits, so no atomics are needed), and
+  // each key's rank among the warp's keys of its digit (two 16-bit ranks
+  // per word), which the scatter below reuses
+  u32 wr[RIPT / 2];
 #pragma unroll
   for (int r = 0; r < RIPT; ++r) {
     const u64 e = wbase + (u64)r * 32 + lane;
     const bool valid = e < n;
     const u32 dg = valid ? (u32)(kr[r] >> shift) & mask : 0xffffffffu;
     const u32 peers = digit_peers(dg, valid);
+    const u32 rk = (valid ? s_w[warp][dg] : 0u) + __popc(peers & lt);
+    if (r & 1) wr[r / 2] |= rk << 16;
+    else wr[r / 2] = rk;
+    __syncwarp();
     if (valid && lane == __ffs(peers) - 1) s_w[warp][dg] += __popc(peers);
     __syncwarp();
   }
@@ -395,23 +402,19 @@ __global__ void __launch_bounds__(RT, 2) k_sort_pass(const K* __restrict__ kin, 
     s_base[tid] = gofs[tid] + excl;
   }
   __syncthreads();
-  // stable scatter, in the order of the count pass
+  // stable scatter: a key goes to its digit's start in the output, plus its
+  // warp's start within the tile's keys of that digit, plus its rank within
+  // the warp's keys of that digit (from the count pass)
 #pragma unroll
   for (int r = 0; r < RIPT; ++r) {
     const u64 e = wbase + (u64)r * 32 + lane;
-    const bool valid = e < n;
+    if (e >= n) continue;
     const K key = kr[r];
-    const u32 val = vr[r];
-    const u32 dg = valid ? (u32)(key >> shift) & mask : 0xffffffffu;
-    const u32 peers = digit_peers(dg, valid);
-    u32 pos = 0;
-    if (valid) pos = s_base[dg] + s_w[warp][dg] + __popc(peers & lt);
-    __syncwarp();
-    if (valid && lane == __ffs(peers) - 1) s_w[warp][dg] += __popc(peers);
-    __syncwarp();
-    if (valid && pos < n) {  // always, unless a look-back wait gave up (then err is set)
+    const u32 dg = (u32)(key >> shift) & mask;
+    const u32 pos = s_base[dg] + s_w[warp][dg] + ((wr[r / 2] >> (16 * (r & 1))) & 0xffffu);
+    if (pos < n) {  // always, unless a look-back wait gave up (then err is set)
       kout[pos] = key;
-      vout[pos] = val;
+      vout[pos] = vr[r];
     }
   }
 }
