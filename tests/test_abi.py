@@ -1,6 +1,6 @@
 """Host-side checks of the C-ABI library that need no GPU: it builds for
-sm_103a, loads, exports every function include/skyline.h declares, and its
-parameter struct has the layout the binding assumes."""
+sm_103a, loads, exports every function include/skyline.h declares, and
+every struct of the header has the layout the binding assumes."""
 import ctypes
 import os
 import re
@@ -62,3 +62,32 @@ def test_library_is_built_for_sm_103a():
     from paper_2411_14968_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
     assert os.path.exists(build.LIB_PATH)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct of the C ABI has, field by field, the offset and size the
+    ctypes binding assumes: a small C program compiled against
+    include/skyline.h prints sizeof and offsetof of each."""
+    import shutil
+    import subprocess
+    from paper_2411_14968_gb300 import native
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {"sky_params": native.SkyParams, "sky_stats": native.SkyStats, "sky_query": native.SkyQuery,
+               "sky_serve_config": native.SkyServeConfig, "sky_ticket_info": native.SkyTicketInfo}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "skyline.h"', "int main(void) {"]
+    want = []
+    for cname, cls in structs.items():
+        lines.append(f'  printf("%zu\\n", sizeof({cname}));')
+        want.append(ctypes.sizeof(cls))
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({cname}, {f}));')
+            want.append(getattr(cls, f).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert got == want
