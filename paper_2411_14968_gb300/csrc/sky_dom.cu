@@ -270,18 +270,23 @@ __device__ __forceinline__ bool dominates_u(const float4* __restrict__ upts, u32
 }
 
 // Tests the warp's candidates against u[lo..hi): 64 entries at a time are
-// staged as 32 dominator pairs in the warp's shared buffer sp (64 uint4; an
-// odd tail is padded with +inf images), then scanned with broadcast shared
-// loads.  Returns when every candidate is dead or the range is done.
+// staged as 32 dominator pairs in the warp's shared buffer sp (64 uint4; a
+// tail is padded with +inf images), then scanned with broadcast shared
+// loads, two pairs per step; the next 64 entries are loaded from global
+// memory while the current ones are scanned.  Returns when every candidate
+// is dead or the range is done.
 template <int D>
 __device__ void ns_scan_range(const NoSeqArgs& a, u32 lo, u32 hi, uint4* sp, NCand<D>& c) {
   const int lane = threadIdx.x & 31;
+  const uint4 z = make_uint4(INF2, INF2, INF2, INF2);
+  uint4 p0, p1;  // this lane's two entries of the next stage
+  {
+    const u32 e0 = lo + 2 * lane;
+    p0 = e0 < hi ? __ldg(a.uhc + e0) : z;
+    p1 = e0 + 1 < hi ? __ldg(a.uhc + e0 + 1) : z;
+  }
   for (u32 j0 = lo; j0 < hi; j0 += 64) {
     {
-      const u32 e0 = j0 + 2 * lane, e1 = e0 + 1;
-      const uint4 z = make_uint4(INF2, INF2, INF2, INF2);
-      const uint4 p0 = e0 < hi ? __ldg(a.uhc + e0) : z;
-      const uint4 p1 = e1 < hi ? __ldg(a.uhc + e1) : z;
       const u32 x0[4] = {p0.x, p0.y, p0.z, p0.w}, x1[4] = {p1.x, p1.y, p1.z, p1.w};
       u32 w[8];
 #pragma unroll
@@ -290,40 +295,53 @@ __device__ void ns_scan_range(const NoSeqArgs& a, u32 lo, u32 hi, uint4* sp, NCa
       sp[2 * lane + 1] = make_uint4(w[4], w[5], w[6], w[7]);
     }
     __syncwarp();
+    if (j0 + 64 < hi) {
+      const u32 e0 = j0 + 64 + 2 * lane;
+      p0 = e0 < hi ? __ldg(a.uhc + e0) : z;
+      p1 = e0 + 1 < hi ? __ldg(a.uhc + e0 + 1) : z;
+    }
     const u32 npairs = min(32u, (hi - j0 + 1) / 2);
-    for (u32 q = 0; q < npairs; ++q) {
-      u32 w[D];
-      const uint4 a0 = sp[2 * q];
-      w[0] = a0.x;
-      if (D > 1) w[1 < D ? 1 : 0] = a0.y;
-      if (D > 2) w[2 < D ? 2 : 0] = a0.z;
-      if (D > 3) w[3 < D ? 3 : 0] = a0.w;
-      if (D > 4) {
-        const uint4 a1 = sp[2 * q + 1];
-        w[4 < D ? 4 : 0] = a1.x;
-        if (D > 5) w[5 < D ? 5 : 0] = a1.y;
-        if (D > 6) w[6 < D ? 6 : 0] = a1.z;
-        if (D > 7) w[7 < D ? 7 : 0] = a1.w;
+    for (u32 q = 0; q < npairs; q += 2) {
+      // pairs q and q + 1 (q + 1 <= 31; past the range it holds +inf images)
+      u32 w[2][D];
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        const uint4 a0 = sp[2 * (q + g)];
+        w[g][0] = a0.x;
+        if (D > 1) w[g][1 < D ? 1 : 0] = a0.y;
+        if (D > 2) w[g][2 < D ? 2 : 0] = a0.z;
+        if (D > 3) w[g][3 < D ? 3 : 0] = a0.w;
+        if (D > 4) {
+          const uint4 a1 = sp[2 * (q + g) + 1];
+          w[g][4 < D ? 4 : 0] = a1.x;
+          if (D > 5) w[g][5 < D ? 5 : 0] = a1.y;
+          if (D > 6) w[g][6 < D ? 6 : 0] = a1.z;
+          if (D > 7) w[g][7 < D ? 7 : 0] = a1.w;
+        }
       }
       u32 acc = 0xffffffffu;
 #pragma unroll
-      for (int r = 0; r < NCand<D>::NR; ++r) acc &= pair_fail<D>(c.t[r], w);
+      for (int g = 0; g < 2; ++g)
+#pragma unroll
+        for (int r = 0; r < NCand<D>::NR; ++r) acc &= pair_fail<D>(c.t[r], w[g]);
       if ((acc & 0x80008000u) != 0x80008000u) {
 #pragma unroll
-        for (int r = 0; r < NCand<D>::NR; ++r) {
-          const u32 x = pair_fail<D>(c.t[r], w);
+        for (int g = 0; g < 2; ++g)
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const u32 jd = j0 + 2 * q + h;
-            if (c.alive[r] && !((x >> (15 + 16 * h)) & 1u) && jd < hi && dominates_u<D>(a.upts, jd, c.pos[r])) {
-              c.alive[r] = false;
+          for (int r = 0; r < NCand<D>::NR; ++r) {
+            const u32 x = pair_fail<D>(c.t[r], w[g]);
 #pragma unroll
-              for (int k = 0; k < D; ++k) c.t[r][k] = NEG_INF2;
+            for (int h = 0; h < 2; ++h) {
+              const u32 jd = j0 + 2 * (q + g) + h;
+              if (c.alive[r] && !((x >> (15 + 16 * h)) & 1u) && jd < hi && dominates_u<D>(a.upts, jd, c.pos[r])) {
+                c.alive[r] = false;
+#pragma unroll
+                for (int k = 0; k < D; ++k) c.t[r][k] = NEG_INF2;
+              }
             }
           }
-        }
       }
-      if ((q & 7) == 7 && !__any_sync(FULL, any_alive(c))) {
+      if ((q & 6) == 6 && !__any_sync(FULL, any_alive(c))) {
         __syncwarp();
         return;
       }
