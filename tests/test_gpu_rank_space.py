@@ -125,7 +125,7 @@ def _oracle_kw(kw, d):
 
 
 @pytest.mark.parametrize("transform", list(TRANSFORMS))
-@pytest.mark.parametrize("d", [2, 4, 6])
+@pytest.mark.parametrize("d", [2, 4, 6, 8])
 def test_rank_images_skyline_matches_oracle(ctx, oracle_mod, transform, d):
     x = np.ascontiguousarray(TRANSFORMS[transform](datagen.anticorrelated(6000, d, 70 + d)), dtype=np.float32)
     for kw in SCHEMES:
