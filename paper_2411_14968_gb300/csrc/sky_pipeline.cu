@@ -314,6 +314,7 @@ struct Work {
   size_t tab_off = 0;        // angular table in the pinned staging (words)
   bool pid_dev = false;      // out_pid / out_stage are device memory
   bool stage_dev = false;
+  int copy_ev = -1;          // event of the input's copy to the device (host input)
 };
 
 #define CK(expr)                                                                       \
@@ -370,6 +371,7 @@ Runner::~Runner() {
     if (e) cudaEventDestroy(e);
   if (gate_ev_) cudaEventDestroy(gate_ev_);
   if (fork_ev_) cudaEventDestroy(fork_ev_);
+  for (auto e : copy_ev_) cudaEventDestroy(e);
   for (int k = 0; k < NAUX; ++k) {
     if (aux_[k]) {
       cudaStreamSynchronize(aux_[k]);
@@ -617,19 +619,35 @@ sky_status Runner::enqueue(BatchState& B) {
   };
   auto qstream = [&](const Work& w) -> cudaStream_t { return multi ? aux_[(&w - ws.data()) % NAUX] : stream; };
   record(0, B);
-  // a host input's copy to the device runs on its query's stream at the
-  // start of the partition phase, so that later queries' copies overlap
-  // earlier queries' partitioning
   record(1, B);
 
   // ---- Partition(r, p): keys, sort, gather (Algorithm 2 first phase)
   CK(fork());
+  // Host inputs are copied to the device one after another on the main
+  // stream, in query order, each at the whole copy bandwidth, and a query's
+  // partitioning waits for its own copy only: later copies overlap earlier
+  // queries' partitioning (copies issued on every query's stream at once
+  // would share the bandwidth and all end together).
+  {
+    size_t k = 0;
+    for (auto& w : ws) {
+      if (w.q->n == 0 || !w.pl.x_on_host) continue;
+      if (k == copy_ev_.size()) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        copy_ev_.push_back(e);
+      }
+      CK(cudaMemcpyAsync(w.b.X, w.q->points, w.q->n * w.q->d * sizeof(float), cudaMemcpyHostToDevice, stream));
+      CK(cudaEventRecord(copy_ev_[k], stream));
+      w.copy_ev = (int)k++;
+    }
+  }
   for (auto& w : ws) {
     if (w.q->n == 0) continue;
     const cudaStream_t st = qstream(w);
     w.X = w.q->points;
     if (w.pl.x_on_host) {
-      CK(cudaMemcpyAsync(w.b.X, w.q->points, w.q->n * w.q->d * sizeof(float), cudaMemcpyHostToDevice, st));
+      CK(cudaStreamWaitEvent(st, copy_ev_[w.copy_ev], 0));
       w.X = w.b.X;
     }
     const Plan& pl = w.pl;

@@ -96,6 +96,7 @@ class Runner {
   static constexpr int NAUX = 4;   // streams the per-query work of a batch is spread over
   cudaStream_t aux_[NAUX] = {};
   cudaEvent_t fork_ev_ = nullptr;
+  std::vector<cudaEvent_t> copy_ev_;  // one per host input of a batch (grown on demand)
   cudaEvent_t join_ev_[NAUX] = {};
   sky_status ensure_ws(size_t bytes);
   sky_status ensure_pinned(size_t words);
