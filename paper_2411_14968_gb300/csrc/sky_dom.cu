@@ -219,28 +219,29 @@ __device__ __forceinline__ u32 pair_fail(const u32 (&t)[D], const u32 (&w)[D]) {
   return x;
 }
 
-template <int D>
+// A lane's NoSeq candidates in NR slots: ns_r(D) when a group is loaded,
+// fewer once its live candidates have been compacted.
+template <int D, int NR>
 struct NCand {
-  static constexpr int NR = ns_r(D);
   u32 t[NR][D];   // duplicated FP16 images (-inf when dead)
   u32 pos[NR];    // position in u
   bool alive[NR];
   bool was[NR];
 };
 
-template <int D>
-__device__ __forceinline__ bool any_alive(const NCand<D>& c) {
-  bool a = false;
+template <int D, int NR>
+__device__ __forceinline__ u32 ns_live(const NCand<D, NR>& c) {
+  u32 n = 0;
 #pragma unroll
-  for (int r = 0; r < NCand<D>::NR; ++r) a |= c.alive[r];
-  return a;
+  for (int r = 0; r < NR; ++r) n += __popc(__ballot_sync(FULL, c.alive[r]));
+  return n;
 }
 
 // Loads the group's candidates at u positions base + r * 32 + lane < end.
-template <int D>
-__device__ __forceinline__ void ns_load(const NoSeqArgs& a, u32 base, u32 end, int lane, NCand<D>& c) {
+template <int D, int NR>
+__device__ __forceinline__ void ns_load(const NoSeqArgs& a, u32 base, u32 end, int lane, NCand<D, NR>& c) {
 #pragma unroll
-  for (int r = 0; r < NCand<D>::NR; ++r) {
+  for (int r = 0; r < NR; ++r) {
     const u32 pos = base + r * 32 + lane;
     const bool ok = pos < end && ld_cg_u8(a.ualive + pos);
     const uint4 h = ok ? __ldg(a.uhc + pos) : make_uint4(0u, 0u, 0u, 0u);
@@ -251,6 +252,57 @@ __device__ __forceinline__ void ns_load(const NoSeqArgs& a, u32 base, u32 end, i
 #pragma unroll
     for (int k = 0; k < D; ++k) c.t[r][k] = ok ? __byte_perm(w[k / 2], 0u, (k & 1) ? 0x3232u : 0x1010u) : NEG_INF2;
   }
+}
+
+// Records the kills of the lane's slots (alive when loaded, dead now).
+template <int D, int NR>
+__device__ __forceinline__ void ns_write_kills(const NoSeqArgs& a, const NCand<D, NR>& c) {
+#pragma unroll
+  for (int r = 0; r < NR; ++r)
+    if (c.was[r] && !c.alive[r]) a.ualive[c.pos[r]] = 0;
+}
+
+// Moves the warp's live candidates of a (at most 32 x NB of them) into NB
+// slots per lane, slot-major, through the warp's shared scratch (sc: images,
+// one uint4 per candidate, sp: positions); a's kills are recorded first.
+template <int D, int NA, int NB>
+__device__ __forceinline__ void ns_compact(const NoSeqArgs& a, const NCand<D, NA>& ca, NCand<D, NB>& cb, uint4* sc,
+                                           u32* sp) {
+  const int lane = threadIdx.x & 31;
+  const u32 lt = (1u << lane) - 1u;
+  ns_write_kills(a, ca);
+  u32 k0 = 0;
+#pragma unroll
+  for (int r = 0; r < NA; ++r) {
+    const u32 m = __ballot_sync(FULL, ca.alive[r]);
+    if (ca.alive[r]) {
+      const u32 k = k0 + __popc(m & lt);
+      u32 w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const u32 lo = 2 * q < D ? ca.t[r][2 * q < D ? 2 * q : 0] : 0u;
+        const u32 hi = 2 * q + 1 < D ? ca.t[r][2 * q + 1 < D ? 2 * q + 1 : 0] : 0u;
+        w[q] = __byte_perm(lo, hi, 0x5410u);
+      }
+      sc[k] = make_uint4(w[0], w[1], w[2], w[3]);
+      sp[k] = ca.pos[r];
+    }
+    k0 += __popc(m);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    const u32 k = r * 32 + lane;
+    const bool v = k < k0;
+    cb.alive[r] = v;
+    cb.was[r] = v;
+    cb.pos[r] = v ? sp[k] : 0u;
+    const uint4 h = v ? sc[k] : make_uint4(0u, 0u, 0u, 0u);
+    const u32 w[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+    for (int q = 0; q < D; ++q) cb.t[r][q] = v ? __byte_perm(w[q / 2], 0u, (q & 1) ? 0x3232u : 0x1010u) : NEG_INF2;
+  }
+  __syncwarp();
 }
 
 // Def. 1 on the FP32 attributes: does u[j] dominate u[i]?
@@ -273,10 +325,13 @@ __device__ __forceinline__ bool dominates_u(const float4* __restrict__ upts, u32
 // staged as 32 dominator pairs in the warp's shared buffer sp (64 uint4; a
 // tail is padded with +inf images), then scanned with broadcast shared
 // loads, two pairs per step; the next 64 entries are loaded from global
-// memory while the current ones are scanned.  Returns when every candidate
-// is dead or the range is done.
-template <int D>
-__device__ void ns_scan_range(const NoSeqArgs& a, u32 lo, u32 hi, uint4* sp, NCand<D>& c) {
+// memory while the current ones are scanned.  Every 16 entries the warp
+// counts its live candidates and stops when none is left or when they fit
+// in half the slots (the caller compacts them and goes on with fewer).
+// Returns the position reached (every entry before it has been tested);
+// *n_live = live candidates.
+template <int D, int NR>
+__device__ u32 ns_scan_range(const NoSeqArgs& a, u32 lo, u32 hi, uint4* sp, NCand<D, NR>& c, u32* n_live) {
   const int lane = threadIdx.x & 31;
   const uint4 z = make_uint4(INF2, INF2, INF2, INF2);
   uint4 p0, p1;  // this lane's two entries of the next stage
@@ -323,12 +378,12 @@ __device__ void ns_scan_range(const NoSeqArgs& a, u32 lo, u32 hi, uint4* sp, NCa
 #pragma unroll
       for (int g = 0; g < 2; ++g)
 #pragma unroll
-        for (int r = 0; r < NCand<D>::NR; ++r) acc &= pair_fail<D>(c.t[r], w[g]);
+        for (int r = 0; r < NR; ++r) acc &= pair_fail<D>(c.t[r], w[g]);
       if ((acc & 0x80008000u) != 0x80008000u) {
 #pragma unroll
         for (int g = 0; g < 2; ++g)
 #pragma unroll
-          for (int r = 0; r < NCand<D>::NR; ++r) {
+          for (int r = 0; r < NR; ++r) {
             const u32 x = pair_fail<D>(c.t[r], w[g]);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -341,14 +396,64 @@ __device__ void ns_scan_range(const NoSeqArgs& a, u32 lo, u32 hi, uint4* sp, NCa
             }
           }
       }
-      if ((q & 6) == 6 && !__any_sync(FULL, any_alive(c))) {
-        __syncwarp();
-        return;
+      if ((q & 6) == 6) {
+        const u32 n = ns_live(c);
+        if (n == 0 || (NR > 1 && n <= 32u * (NR / 2))) {
+          __syncwarp();
+          *n_live = n;
+          return min(j0 + 2 * (q + 2), hi);
+        }
       }
     }
     __syncwarp();  // the buffer is restaged only after every lane's reads
-    if (!__any_sync(FULL, any_alive(c))) return;
   }
+  *n_live = ns_live(c);
+  return hi;
+}
+
+// The rest of one item from u position pos: every partition j of u[pos,
+// bhi) that is a potential dominator of partition i, cut at the group's
+// largest score fmax (u_j is sorted by score, so later points cannot
+// dominate), scanned with the NR-slot candidates; when they fit in fewer
+// slots they are compacted and the item goes on with those.  Records the
+// kills.
+template <int D, int NR>
+__device__ void ns_rest(const NoSeqArgs& a, u32 i, float fmax, u32 pos, u32 bhi, NCand<D, NR>& c, u32 n,
+                        uint4* sp, uint4* sc, u32* spos) {
+  while (pos < bhi && n > 0) {
+    // partition j holding u position pos
+    u32 l2 = 0, h2 = a.P;
+    while (h2 - l2 > 1) {
+      u32 mid = (l2 + h2) >> 1;
+      if (__ldg(a.useg + mid) <= pos) l2 = mid;
+      else h2 = mid;
+    }
+    const u32 j = l2;
+    const u32 jend = min(__ldg(a.useg + j + 1), bhi);
+    if (in_pd(a, i, j)) {
+      u32 lo3 = pos, hi3 = jend;
+      while (lo3 < hi3) {
+        u32 mid = lo3 + ((hi3 - lo3) >> 1);
+        if (__ldg(a.uscore + mid) <= fmax) lo3 = mid + 1;
+        else hi3 = mid;
+      }
+      const u32 cut = lo3;
+      if (cut > pos) {
+        const u32 reached = ns_scan_range<D, NR>(a, pos, cut, sp, c, &n);
+        if (reached < cut) {
+          if (n == 0) break;
+          if constexpr (NR > 1) {
+            NCand<D, NR / 2> c2;
+            ns_compact<D, NR, NR / 2>(a, c, c2, sc, spos);
+            ns_rest<D, NR / 2>(a, i, fmax, reached, bhi, c2, n, sp, sc, spos);
+            return;
+          }
+        }
+      }
+    }
+    pos = jend;
+  }
+  ns_write_kills(a, c);
 }
 
 // Items: (group of u_i, dominator block of u).  gpre[P + 1]: prefix of the
@@ -356,7 +461,10 @@ __device__ void ns_scan_range(const NoSeqArgs& a, u32 lo, u32 hi, uint4* sp, NCa
 template <int D>
 __global__ void __launch_bounds__(THREADS) k_noseq(NoSeqArgs a, const u32* __restrict__ gpre, const u32* nu_dev,
                                                    u32* counter) {
+  constexpr int NR0 = ns_r(D);
   __shared__ uint4 s_pairs[WARPS][64];
+  __shared__ uint4 s_cimg[WARPS][32 * NR0];  // compaction scratch: images
+  __shared__ u32 s_cpos[WARPS][32 * NR0];    // and positions
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 nu = *nu_dev;
   const u32 ngroups = gpre[a.P];
@@ -380,53 +488,30 @@ __global__ void __launch_bounds__(THREADS) k_noseq(NoSeqArgs a, const u32* __res
       }
       const u32 i = lo;
       const u32 ibeg = __ldg(a.useg + i), iend = __ldg(a.useg + i + 1);
-      constexpr u32 NGS = 32 * NCand<D>::NR;  // candidates per group
+      constexpr u32 NGS = 32 * NR0;  // candidates per group
       const u32 base = ibeg + (G - __ldg(gpre + i)) * NGS;
       const u32 gend = min(base + NGS, iend);
       const float fmax = __ldg(a.uscore + gend - 1);
-      // dominator block [blo, bhi) of u; visit the partitions it overlaps
+      // dominator block [blo, bhi) of u: its first partition that holds
+      // potential dominators (the candidates are loaded only if there is one)
       const u32 blo = b * DB, bhi = min(blo + DB, nu);
-      NCand<D> c;
-      bool loaded = false;
       u32 pos = blo;
       while (pos < bhi) {
-        // partition j holding u position pos
         u32 l2 = 0, h2 = a.P;
         while (h2 - l2 > 1) {
           u32 mid = (l2 + h2) >> 1;
           if (__ldg(a.useg + mid) <= pos) l2 = mid;
           else h2 = mid;
         }
-        const u32 j = l2;
-        const u32 jend = min(__ldg(a.useg + j + 1), bhi);
-        if (in_pd(a, i, j)) {
-          // u_j is sorted by score: only points with score <= fmax can dominate
-          u32 cut = jend;
-          {
-            u32 lo3 = pos, hi3 = jend;
-            while (lo3 < hi3) {
-              u32 mid = lo3 + ((hi3 - lo3) >> 1);
-              if (__ldg(a.uscore + mid) <= fmax) lo3 = mid + 1;
-              else hi3 = mid;
-            }
-            cut = lo3;
-          }
-          if (cut > pos) {
-            if (!loaded) {
-              ns_load<D>(a, base, gend, lane, c);
-              loaded = true;
-            }
-            if (!__any_sync(FULL, any_alive(c))) break;
-            ns_scan_range<D>(a, pos, cut, s_pairs[warp], c);
-          }
-        }
-        pos = jend;
+        if (in_pd(a, i, l2) && __ldg(a.uscore + pos) <= fmax) break;
+        pos = min(__ldg(a.useg + l2 + 1), bhi);
       }
-      if (loaded) {
-#pragma unroll
-        for (int r = 0; r < NCand<D>::NR; ++r)
-          if (c.was[r] && !c.alive[r]) a.ualive[c.pos[r]] = 0;
-      }
+      if (pos >= bhi) continue;
+      NCand<D, NR0> c;
+      ns_load<D, NR0>(a, base, gend, lane, c);
+      const u32 n = ns_live(c);
+      if (n == 0) continue;
+      ns_rest<D, NR0>(a, i, fmax, pos, bhi, c, n, s_pairs[warp], s_cimg[warp], s_cpos[warp]);
     }
   }
 }
