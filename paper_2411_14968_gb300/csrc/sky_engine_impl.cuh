@@ -1404,6 +1404,11 @@ cudaError_t engine_run_variant<WARPS, R>(const SegDesc* segs_dev, u32 nseg, cons
   if (per_sm <= 0) return cudaErrorInvalidConfiguration;
   if (!g_sms) g_sms = device_sm_count();
   unsigned grid = (unsigned)(g_sms * per_sm);
+  // a small launch (few tiles in any phase) gets fewer CTAs: any grid size
+  // is correct (no CTA waits for one that is not resident), and the CTAs
+  // that would find no work still cost their scheduling and exit
+  const u64 want = 4 * w.tcap > 16 ? 4 * w.tcap : 16;
+  if (want < grid) grid = (unsigned)want;
   e = cudaMemsetAsync(w.ctl, 0, ENGINE_CTL_WORDS * sizeof(u32), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.tasks, 0, w.task_cap * sizeof(Task), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(w.tstat, 0, w.tcap * sizeof(u32), st);
