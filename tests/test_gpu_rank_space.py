@@ -196,3 +196,28 @@ def test_rank_images_graph_serving_autotune(ctx, oracle_mod, torch_cuda):
     tuned, ms = ctx.autotune(x0[0], params=ps[0], max_trials=6)
     assert ms > 0 and tuned.images == native.IMAGES["ranks"]
     np.testing.assert_array_equal(ctx.skyline(x0[0], params=tuned), want0[0])
+
+
+def test_rank_images_extreme_values(ctx, oracle_mod):
+    """Rank images of columns holding +-inf, -0.0 beside +0.0, subnormals,
+    the largest finite values and long runs of one value: the same skyline,
+    partitions and stage codes as the oracle's, and the same ranks."""
+    rng = np.random.default_rng(95)
+    x = datagen.anticorrelated(5000, 5, 95)
+    special = np.array([np.inf, -np.inf, -0.0, 0.0, 1e-40, -1e-40, 3.4e38, -3.4e38, 7.0], np.float32)
+    mask = rng.random(x.shape) < 0.05
+    x[mask] = rng.choice(special, size=int(mask.sum()))
+    x[:300, 1] = np.float32(0.25)  # a long run of one value
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    want_r, want_d = oracle_mod.dense_ranks(x)
+    r, dist, _ = ctx.rank_space(x)
+    np.testing.assert_array_equal(dist, want_d)
+    np.testing.assert_array_equal(r, want_r)
+    for kw, okw in ((dict(scheme="none"), dict(scheme=oracle_mod.NONE)),
+                    (dict(scheme="sliced", p=8, merge="noseq"), dict(scheme=oracle_mod.SLICED, p=8, merge=1)),
+                    (dict(scheme="random", p=16, rep="sorted"), dict(scheme=oracle_mod.RANDOM, p=16, rep=1))):
+        want = oracle_mod.partitioned(x, **okw)
+        idx, pid, stage = ctx.skyline(x, images="ranks", with_diag=True, **kw)
+        np.testing.assert_array_equal(idx, want["indices"], err_msg=str(kw))
+        np.testing.assert_array_equal(pid, want["pid"], err_msg=str(kw))
+        np.testing.assert_array_equal(stage, want["stage"], err_msg=str(kw))
