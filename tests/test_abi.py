@@ -42,6 +42,9 @@ def test_params_layout_and_defaults(lib):
     assert p.scheme == native.SCHEMES["none"] and p.num_partitions == 1
     assert list(p.slices) == [1] * 8 and p.grid_filter == 1 and p.reps_per_partition == 1
     assert p.merge == 0 and p.exec == 0 and p.rep == 0
+    # engine knobs 0 = built-in defaults; images of the values by default
+    assert p.chunk_min == p.chunk_max == p.chunk_alpha_x4 == p.dom_block == 0
+    assert p.engine_warps == p.engine_cands == 0 and p.images == native.IMAGES["values"]
 
 
 def test_status_strings(lib):
