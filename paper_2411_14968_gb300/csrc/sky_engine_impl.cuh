@@ -51,9 +51,11 @@
 // and a segment's long phase never holds up the others.
 //
 // Dominance test.  Every point carries, next to its FP32 attributes, their
-// round-down FP16 images packed two per 32-bit word.  Round-down is monotone,
-// so if any FP16 image of w exceeds t's, then w exceeds t in that attribute
-// and cannot dominate t: the FP16 test (the signs of f16x2 differences; a
+// 16-bit images packed two per 32-bit word: the round-down FP16 values, or
+// the rank codes of sky_rank.cu (finite non-negative FP16 bit patterns).
+// Both are non-decreasing in the value, so if any image of w exceeds t's,
+// then w exceeds t in that attribute and cannot dominate t: the FP16 test
+// (the signs of f16x2 differences; a
 // candidate's images are duplicated per word and staged dominators come in
 // pairs, so one subtraction tests one attribute of two pairs) rejects
 // exactly, and only pairs it passes are tested in FP32 (Def. 1).  A warp
