@@ -14,10 +14,12 @@
 // large or very small magnitudes).
 //
 // One column at a time: sort (value key, index) pairs by the value's
-// monotone unsigned image (the radix sort of sky_prims.cu), flag the sorted
-// positions whose value differs from the previous one, an inclusive scan of
-// the flags gives rank + 1 (and, as its total, the number of distinct
-// values), and a scatter writes rank and code at the point's own index.
+// monotone unsigned image (the radix sort of sky_prims.cu, on 32-bit keys),
+// flag the sorted positions whose value differs from the previous one, an
+// inclusive scan of the flags gives rank + 1 (and, as its total, the number
+// of distinct values), and a scatter writes the rank at the point's own
+// index of the column's rank array.  One last kernel then writes ranks and
+// codes row-major from the column arrays.
 #include <cstring>
 #include <string>
 #include "sky_pipeline.cuh"
