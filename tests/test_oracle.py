@@ -558,3 +558,29 @@ def test_dense_ranks_keep_the_skyline(oracle_mod, kind, d):
         assert (ranks.max(axis=0) + 1 == distinct).all()
         np.testing.assert_array_equal(oracle_mod.skyline_indices(ranks.astype(np.float32)),
                                       oracle_mod.skyline_indices(pts))
+
+
+def test_dense_ranks_and_skyline_properties_hypothesis(oracle_mod):
+    """Generated inputs with infinities, signed zeros, subnormals and many
+    ties: the dense ranks equal a Python count of smaller distinct values,
+    and the skyline of the ranks is the brute-force skyline of the values."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+    values = st.sampled_from([0.0, -0.0, 1e-40, -1e-40, 0.5, 1.0, 2.0, -3.0, 3.4e38, float("inf"), float("-inf")])
+
+    @hyp.settings(max_examples=60, deadline=None)
+    @hyp.given(st.integers(1, 5).flatmap(
+        lambda d: st.lists(st.lists(values, min_size=d, max_size=d), min_size=1, max_size=40)))
+    def check(rows):
+        x = np.array(rows, np.float32)
+        ranks, distinct = oracle_mod.dense_ranks(x)
+        for a in range(x.shape[1]):
+            vals = {float(v) for v in x[:, a]}
+            assert distinct[a] == len(vals)
+            for i in range(x.shape[0]):
+                assert ranks[i, a] == sum(1 for v in vals if v < float(x[i, a]))
+        want = np.nonzero(oracle_mod.skyline_brute(x))[0]
+        np.testing.assert_array_equal(oracle_mod.skyline_indices(ranks.astype(np.float32)), want)
+        np.testing.assert_array_equal(oracle_mod.skyline_indices(x), want)
+
+    check()
