@@ -3,7 +3,8 @@ each variant the benchmark times -- on the 1,000,000-point anticorrelated
 d = 6 workload (seed 1: workcounts_ant_1m_d6.json) and on the 2,000,000-point
 skewed d = 6 workload (seed 4, Angular (4,4,2,2,2) on x / column max with
 Sorted representatives, sequential final phase:
-workcounts_skewed_2m_d6.json), and on the 200,000-point skewed workload
+workcounts_skewed_2m_d6.json; NoSeq final phase:
+workcounts_skewed_2m_d6_noseq.json), and on the 200,000-point skewed workload
 (seed 4) with the NoSeq final phase (workcounts_skewed_200k_d6.json).
 
 The count of one variant is the number of pairwise dominance tests the
@@ -42,6 +43,11 @@ WORKLOADS = {
     }),
     "skewed_2m_d6": ("skewed", 2_000_000, 6, 4, {
         "angular_rep": dict(scheme=O.ANGULAR, slices=[4, 4, 2, 2, 2], normalize=True, rep=O.REP_SORTED),
+    }),
+    # the skewed workload with the NoSeq final phase (merge_tests = NoSeq's tests)
+    "skewed_2m_d6_noseq": ("skewed", 2_000_000, 6, 4, {
+        "angular_rep_noseq": dict(scheme=O.ANGULAR, slices=[4, 4, 2, 2, 2], normalize=True, rep=O.REP_SORTED,
+                                  merge=O.MERGE_NOSEQ),
     }),
     # the case the NoSeq kernel's profile runs (merge_tests = NoSeq's tests)
     "skewed_200k_d6": ("skewed", 200_000, 6, 4, {
