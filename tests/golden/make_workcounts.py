@@ -4,8 +4,11 @@ d = 6 workload (seed 1: workcounts_ant_1m_d6.json) and on the 2,000,000-point
 skewed d = 6 workload (seed 4, Angular (4,4,2,2,2) on x / column max with
 Sorted representatives, sequential final phase:
 workcounts_skewed_2m_d6.json; NoSeq final phase:
-workcounts_skewed_2m_d6_noseq.json), and on the 200,000-point skewed workload
-(seed 4) with the NoSeq final phase (workcounts_skewed_200k_d6.json).
+workcounts_skewed_2m_d6_noseq.json), on the 200,000-point skewed workload
+(seed 4) with the NoSeq final phase (workcounts_skewed_200k_d6.json), and on
+the 4,000,000-point quantised independent d = 8 workload (seed 3, Grid m = 2
+and Random p = 256 with seed 11, as the benchmark's configuration run:
+workcounts_indep_4m_d8.json).
 
 The count of one variant is the number of pairwise dominance tests the
 plain CPU oracle makes (SFS window tests of Algorithm 1 in every partition,
@@ -43,6 +46,11 @@ WORKLOADS = {
     }),
     "skewed_2m_d6": ("skewed", 2_000_000, 6, 4, {
         "angular_rep": dict(scheme=O.ANGULAR, slices=[4, 4, 2, 2, 2], normalize=True, rep=O.REP_SORTED),
+    }),
+    # the quantised independent workload, N = 4M, d = 8: Grid m = 2 and Random p = 256
+    "indep_4m_d8": ("independent", 4_000_000, 8, 3, {
+        "grid": dict(scheme=O.GRID, slices=[2] * 8),
+        "random": dict(scheme=O.RANDOM, p=256, seed=11),
     }),
     # the skewed workload with the NoSeq final phase (merge_tests = NoSeq's tests)
     "skewed_2m_d6_noseq": ("skewed", 2_000_000, 6, 4, {
