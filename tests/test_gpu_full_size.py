@@ -70,8 +70,16 @@ def test_anticorrelated_1m_d6_bench_config(ctx):
 
 @pytest.mark.parametrize("name", ["independent_q_4m_d8", "correlated_q_4m_d8"])
 def test_quantised_4m_d8_grid_vs_random(ctx, name):
-    _check_batch(ctx, name, [dict(scheme="grid", slices=[2] * 8), dict(scheme="random", p=256, seed=11),
-                             dict(scheme="grid", slices=[2] * 8, merge="noseq")])
+    from paper_2411_14968_gb300 import native
+    variants = [dict(scheme="grid", slices=[2] * 8), dict(scheme="random", p=256, seed=11)]
+    xt = _check_batch(ctx, name, variants + [dict(scheme="grid", slices=[2] * 8, merge="noseq")])
+    if name == "independent_q_4m_d8":
+        # |u| equals the oracle's: 4M points' partitions (Random's ranks of
+        # SplitMix64 keys included) and local skylines are exact too
+        wc = json.load(open(os.path.join(HERE, "golden", "workcounts_indep_4m_d8.json")))["variants"]
+        for key, kw in zip(("grid", "random"), variants):
+            ctx.skyline(xt, params=native.make_params(**kw))
+            assert ctx.stats()["local_union"] == wc[key]["local_union"], key
 
 
 def test_skewed_angular_p128_reps(ctx):
@@ -86,8 +94,13 @@ def test_skewed_2m_d6_bench_config(ctx):
     # oracle's Algorithm 2 with NoSeq over every host core, pinned equal to
     # the plain SFS on smaller inputs.  Every partitioning and merge must
     # return that set exactly (Prop. 1, Prop. 2).
+    from paper_2411_14968_gb300 import native
     sl = [4, 4, 2, 2, 2]
-    _check_batch(ctx, "skewed_2m_d6", [dict(scheme="angular", slices=sl, normalize=True, rep="sorted"),
-                                       dict(scheme="angular", slices=sl, normalize=True, rep="sorted",
-                                            merge="noseq"),
-                                       dict(scheme="sliced", p=128), dict(scheme="random", p=128, seed=9)])
+    xt = _check_batch(ctx, "skewed_2m_d6", [dict(scheme="angular", slices=sl, normalize=True, rep="sorted"),
+                                            dict(scheme="angular", slices=sl, normalize=True, rep="sorted",
+                                                 merge="noseq"),
+                                            dict(scheme="sliced", p=128), dict(scheme="random", p=128, seed=9)])
+    # |u| of the benchmark's skewed configuration equals the oracle's
+    wc = json.load(open(os.path.join(HERE, "golden", "workcounts_skewed_2m_d6.json")))["variants"]["angular_rep"]
+    ctx.skyline(xt, params=native.make_params(scheme="angular", slices=sl, normalize=True, rep="sorted"))
+    assert ctx.stats()["local_union"] == wc["local_union"]
