@@ -8,7 +8,8 @@ workcounts_skewed_2m_d6_noseq.json), on the 200,000-point skewed workload
 (seed 4) with the NoSeq final phase (workcounts_skewed_200k_d6.json), and on
 the 4,000,000-point quantised independent d = 8 workload (seed 3, Grid m = 2
 and Random p = 256 with seed 11, as the benchmark's configuration run:
-workcounts_indep_4m_d8.json).
+workcounts_indep_4m_d8.json; the correlated one likewise:
+workcounts_corr_4m_d8.json).
 
 The count of one variant is the number of pairwise dominance tests the
 plain CPU oracle makes (SFS window tests of Algorithm 1 in every partition,
@@ -49,6 +50,11 @@ WORKLOADS = {
     }),
     # the quantised independent workload, N = 4M, d = 8: Grid m = 2 and Random p = 256
     "indep_4m_d8": ("independent", 4_000_000, 8, 3, {
+        "grid": dict(scheme=O.GRID, slices=[2] * 8),
+        "random": dict(scheme=O.RANDOM, p=256, seed=11),
+    }),
+    # the quantised correlated workload, N = 4M, d = 8: the same two variants
+    "corr_4m_d8": ("correlated", 4_000_000, 8, 3, {
         "grid": dict(scheme=O.GRID, slices=[2] * 8),
         "random": dict(scheme=O.RANDOM, p=256, seed=11),
     }),

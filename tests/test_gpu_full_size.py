@@ -73,13 +73,13 @@ def test_quantised_4m_d8_grid_vs_random(ctx, name):
     from paper_2411_14968_gb300 import native
     variants = [dict(scheme="grid", slices=[2] * 8), dict(scheme="random", p=256, seed=11)]
     xt = _check_batch(ctx, name, variants + [dict(scheme="grid", slices=[2] * 8, merge="noseq")])
-    if name == "independent_q_4m_d8":
-        # |u| equals the oracle's: 4M points' partitions (Random's ranks of
-        # SplitMix64 keys included) and local skylines are exact too
-        wc = json.load(open(os.path.join(HERE, "golden", "workcounts_indep_4m_d8.json")))["variants"]
-        for key, kw in zip(("grid", "random"), variants):
-            ctx.skyline(xt, params=native.make_params(**kw))
-            assert ctx.stats()["local_union"] == wc[key]["local_union"], key
+    # |u| equals the oracle's: 4M points' partitions (Random's ranks of
+    # SplitMix64 keys included) and local skylines are exact too
+    gold = {"independent_q_4m_d8": "workcounts_indep_4m_d8.json", "correlated_q_4m_d8": "workcounts_corr_4m_d8.json"}
+    wc = json.load(open(os.path.join(HERE, "golden", gold[name])))["variants"]
+    for key, kw in zip(("grid", "random"), variants):
+        ctx.skyline(xt, params=native.make_params(**kw))
+        assert ctx.stats()["local_union"] == wc[key]["local_union"], key
 
 
 def test_skewed_angular_p128_reps(ctx):
