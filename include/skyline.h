@@ -337,9 +337,9 @@ sky_status sky_rank_space(sky_ctx* ctx, const float* points, uint64_t n, uint32_
    sky_skyline_ex or sky_skyline_batch call of the context (a batch's sizes
    and counts are sums over its queries, its round counts maxima).  A
    serving ticket: that query's own sizes and counts (Section 3 partitions,
-   filtered points, |u|, |Sky|), with the launches and device times of the
-   batch it ran in (device times only when sky_set_timing was on when the
-   serving loop started); available from completion until long after
+   filtered points, |u|, |Sky|), with the launches, engine test counts and
+   device times of the batch it ran in (device times only when
+   sky_set_timing was on when the serving loop started); available from completion until long after
    sky_wait collects the ticket (the last 4096 collected tickets are kept).
    SKY_EBUSY if the ticket has not completed, SKY_ECANCELLED if it is
    unknown, SKY_EINVAL for NULL arguments. */
