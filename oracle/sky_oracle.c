@@ -19,7 +19,8 @@
  * Readings of places where the paper is silent or garbled (each also listed in
  * the design notes):
  *  - score f(t) = FP32 sum of the attributes, added left to right (§2 monotone
- *    scoring function; a sum is the paper's example of one);
+ *    scoring function; a sum is the paper's example of one); a tuple holding
+ *    both +inf and -inf, whose sum is undefined, scores +inf;
  *  - SFS sort key = (f, x_1, ..., x_d, index): a total order that is a
  *    topological sort of dominance even when f ties (Algorithm 1, §2);
  *  - Grid cell index = sum_i clamp(floor(fl(x_i * m_i)), 0, m_i - 1) * prod_{j<i} m_j
@@ -139,7 +140,10 @@ void orc_dense_ranks(const float *pts, int64_t n, int d, uint32_t *ranks, uint32
 static float score_of(const float *t, int d) {
   float f = t[0];
   for (int a = 1; a < d; ++a) f = f + t[a];
-  return f;
+  /* a tuple holding both +inf and -inf has no sum (inf - inf); it can only
+     dominate tuples that hold +inf in the same attribute, whose sum is +inf
+     or undefined too, so +inf keeps the score monotone under dominance */
+  return f != f ? INFINITY : f;
 }
 
 void orc_scores(const float *pts, int64_t n, int d, float *out) {

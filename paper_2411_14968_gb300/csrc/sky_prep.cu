@@ -21,7 +21,10 @@ __device__ __forceinline__ float score_of(const float (&x)[8]) {
   float f = x[0];
 #pragma unroll
   for (int a = 1; a < D; ++a) f = __fadd_rn(f, x[a]);
-  return f;
+  // a point holding both +inf and -inf has no sum (inf - inf): it scores
+  // +inf, which keeps the score monotone under dominance (such a point
+  // dominates only points holding +inf in the same attribute)
+  return f != f ? __int_as_float(0x7f800000) : f;
 }
 
 // FP16 round-down images of the 8 (padded) attributes, two per word,

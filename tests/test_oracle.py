@@ -584,3 +584,16 @@ def test_dense_ranks_and_skyline_properties_hypothesis(oracle_mod):
         np.testing.assert_array_equal(oracle_mod.skyline_indices(x), want)
 
     check()
+
+
+def test_score_of_a_tuple_with_both_infinities(oracle_mod):
+    # (0, +inf, -inf) has no FP32 sum (inf - inf); it dominates (1, +inf, 0)
+    # (0 <= 1, +inf <= +inf, -inf < 0), so SFS must place it first: its score
+    # is taken as +inf, the score of (1, +inf, 0), and the tie order
+    # (attributes, then index) puts it before; (2, 1, 1) is incomparable
+    x = np.array([[1.0, np.inf, 0.0], [0.0, np.inf, -np.inf], [2.0, 1.0, 1.0]], np.float32)
+    assert oracle_mod.scores(x)[1] == np.inf
+    np.testing.assert_array_equal(np.nonzero(oracle_mod.skyline_brute(x))[0], [1, 2])
+    np.testing.assert_array_equal(oracle_mod.skyline_indices(x), [1, 2])
+    for kw in (dict(scheme=oracle_mod.SLICED, p=2), dict(scheme=oracle_mod.NONE, rep=oracle_mod.REP_SORTED)):
+        np.testing.assert_array_equal(oracle_mod.partitioned(x, **kw)["indices"], [1, 2])
