@@ -597,3 +597,30 @@ def test_score_of_a_tuple_with_both_infinities(oracle_mod):
     np.testing.assert_array_equal(oracle_mod.skyline_indices(x), [1, 2])
     for kw in (dict(scheme=oracle_mod.SLICED, p=2), dict(scheme=oracle_mod.NONE, rep=oracle_mod.REP_SORTED)):
         np.testing.assert_array_equal(oracle_mod.partitioned(x, **kw)["indices"], [1, 2])
+
+
+def test_every_scheme_on_generated_special_values(oracle_mod):
+    """Prop. 1 and Prop. 2 on generated inputs full of infinities, signed
+    zeros, subnormals and ties: every partitioning, representative filter
+    and final phase returns the Def. 1 brute-force skyline."""
+    hyp = pytest.importorskip("hypothesis")
+    st = pytest.importorskip("hypothesis.strategies")
+    O = oracle_mod
+    values = st.sampled_from([0.0, -0.0, 1e-40, -1e-40, 0.25, 0.5, 1.0, 2.0, -3.0, 3.4e38,
+                              float("inf"), float("-inf")])
+
+    @hyp.settings(max_examples=80, deadline=None)
+    @hyp.given(st.integers(2, 5).flatmap(
+        lambda d: st.lists(st.lists(values, min_size=d, max_size=d), min_size=1, max_size=30)))
+    def check(rows):
+        x = np.array(rows, np.float32)
+        d = x.shape[1]
+        want = np.nonzero(O.skyline_brute(x))[0]
+        for kw in (dict(scheme=O.GRID, slices=[2] * d), dict(scheme=O.GRID, slices=[3] * d, grid_filter=False),
+                   dict(scheme=O.ANGULAR, slices=[2] * (d - 1)), dict(scheme=O.RANDOM, p=3, rep=O.REP_REGION),
+                   dict(scheme=O.SLICED, p=4, slice_dim=d - 1, rep=O.REP_SORTED),
+                   dict(scheme=O.GRID, slices=[2] * d, merge=O.MERGE_NOSEQ, rep=O.REP_SORTED),
+                   dict(scheme=O.ANGULAR, slices=[2] * (d - 1), merge=O.MERGE_NOSEQ)):
+            np.testing.assert_array_equal(O.partitioned(x, **kw)["indices"], want, err_msg=str(kw))
+
+    check()
