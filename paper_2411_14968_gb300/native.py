@@ -9,6 +9,7 @@ on the tensor's current stream).
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 import threading
 
@@ -228,6 +229,53 @@ def make_params(scheme="none", p: int = 1, slices=None, normalize=False, slice_d
     return sp
 
 
+# the engine knobs of sky_params that sky_autotune chooses
+KNOBS = ("chunk_min", "chunk_max", "chunk_alpha_x4", "dom_block", "engine_warps", "engine_cands")
+
+
+def tune_key(n: int, d: int, params: SkyParams) -> str:
+    """Key of a tuned-knobs cache entry: the workload's shape -- d, N to the
+    power of two below it, and the method parameters (the knobs excluded)."""
+    rec = {"d": int(d), "log2_n": max(0, int(n).bit_length() - 1), "scheme": int(params.scheme),
+           "p": int(params.num_partitions), "slices": [int(v) for v in list(params.slices)[: int(d)]],
+           "normalize": int(params.normalize), "slice_dim": int(params.slice_dim),
+           "grid_filter": int(params.grid_filter), "rep": int(params.rep),
+           "k": int(params.reps_per_partition), "merge": int(params.merge), "exec": int(params.exec),
+           "images": int(params.images)}
+    return json.dumps(rec, sort_keys=True)
+
+
+class TuneCache:
+    """Tuned engine knobs kept in a JSON file across processes: one entry
+    per tune_key, holding the six knobs and the time they gave."""
+
+    def __init__(self, path: str):
+        self.path = path
+        self.entries = {}
+        if os.path.exists(path):
+            with open(path) as fh:
+                self.entries = json.load(fh)
+
+    def get(self, key: str):
+        return self.entries.get(key)
+
+    def put(self, key: str, params: SkyParams, ms: float):
+        self.entries[key] = {**{k: int(getattr(params, k)) for k in KNOBS}, "ms": float(ms)}
+        self.save()
+
+    def save(self):
+        tmp = f"{self.path}.{os.getpid()}.tmp"
+        with open(tmp, "w") as fh:
+            json.dump(self.entries, fh, indent=1, sort_keys=True)
+        os.replace(tmp, self.path)
+
+    @staticmethod
+    def apply(entry: dict, params: SkyParams) -> SkyParams:
+        for k in KNOBS:
+            setattr(params, k, int(entry[k]))
+        return params
+
+
 def _is_cuda_tensor(x) -> bool:
     return hasattr(x, "is_cuda") and bool(x.is_cuda)
 
@@ -384,16 +432,29 @@ class Context:
             return res[: cnt.value], pid[:n], stage[:n]
         return res[: cnt.value]
 
-    def autotune(self, points, params: SkyParams | None = None, max_trials: int = 0, **kw):
+    def autotune(self, points, params: SkyParams | None = None, max_trials: int = 0, cache=None, **kw):
         """Tunes the engine knobs for this workload (sky_autotune); returns
         (tuned SkyParams, best time in ms).  points: host numpy or CUDA
-        torch float32 [N, d]."""
+        torch float32 [N, d].  cache: a TuneCache or the path of its JSON
+        file; a workload of the same shape (tune_key) found there gets the
+        stored knobs without a trial, and a new one is tuned and stored."""
         if params is None:
             params = make_params(**kw)
         else:
             sp = SkyParams()
             ctypes.memmove(ctypes.byref(sp), ctypes.byref(params), ctypes.sizeof(SkyParams))
             params = sp
+        if cache is not None:
+            if not isinstance(cache, TuneCache):
+                cache = TuneCache(str(cache))
+            n0, d0 = (int(v) for v in points.shape)
+            key = tune_key(n0, d0, params)
+            hit = cache.get(key)
+            if hit is not None:
+                return TuneCache.apply(hit, params), hit["ms"]
+            tuned, ms = self.autotune(points, params=params, max_trials=max_trials)
+            cache.put(key, tuned, ms)
+            return tuned, ms
         if _is_cuda_tensor(points):
             import torch
             points = points.contiguous()
