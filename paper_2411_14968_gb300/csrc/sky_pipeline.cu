@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <nvtx3/nvToolsExt.h>
 #include "sky_pipeline.cuh"
 
 namespace sky {
@@ -588,8 +589,17 @@ sky_status Runner::prepare(BatchState& B, Query* queries, u32 nq, bool graph) {
   return SKY_OK;
 }
 
+// Phase boundaries of a batch: CUDA events (when timing is on) and NVTX
+// ranges on the host thread (one per phase, for a profiler's timeline; the
+// calls do nothing unless a tool is attached).  Boundaries 1..6 open the
+// phases below, 7 (in finish) closes the last; 0 and 8..11 are events only.
 void Runner::record(int i, const BatchState& B) {
   if (timing && !B.graph) cudaEventRecord(ev_[i], stream);
+  static const char* const kPhase[7] = {nullptr, "sky: partition", "sky: filters", "sky: local skylines",
+                                        "sky: final phase", "sky: output", "sky: host copies"};
+  if (B.graph || i < 1 || i > 7) return;
+  if (i >= 2) nvtxRangePop();
+  if (i <= 6) nvtxRangePushA(kPhase[i]);
 }
 
 sky_status Runner::enqueue(BatchState& B) {
