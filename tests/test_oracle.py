@@ -624,3 +624,30 @@ def test_every_scheme_on_generated_special_values(oracle_mod):
             np.testing.assert_array_equal(O.partitioned(x, **kw)["indices"], want, err_msg=str(kw))
 
     check()
+
+
+def _numpy_skyline(x):
+    """Def. 1 written with numpy broadcasting, independent of the oracle's C
+    code: t is dropped iff some s has s <= t in every attribute and s < t in
+    one."""
+    le = (x[:, None, :] <= x[None, :, :]).all(axis=2)   # le[s, t]: s <= t everywhere
+    lt = (x[:, None, :] < x[None, :, :]).any(axis=2)    # lt[s, t]: s < t somewhere
+    dominated = (le & lt).any(axis=0)
+    return np.nonzero(~dominated)[0].astype(np.uint32)
+
+
+@pytest.mark.parametrize("kind,d", [("anticorrelated", 3), ("independent", 5), ("correlated", 7), ("skewed", 4)])
+def test_oracle_against_numpy_def1(oracle_mod, kind, d):
+    x = datagen.make(kind, 1200, d, 50 + d)
+    rng = np.random.default_rng(d)
+    special = np.array([np.inf, -np.inf, -0.0, 0.0, 1e-40], np.float32)
+    y = x.copy()
+    mask = rng.random(y.shape) < 0.02
+    y[mask] = rng.choice(special, size=int(mask.sum()))
+    for pts in (x, y):
+        want = _numpy_skyline(pts)
+        np.testing.assert_array_equal(np.nonzero(oracle_mod.skyline_brute(pts))[0], want)
+        np.testing.assert_array_equal(oracle_mod.skyline_indices(pts), want)
+        r = oracle_mod.partitioned(pts, scheme=oracle_mod.SLICED, p=6, rep=oracle_mod.REP_SORTED,
+                                   merge=oracle_mod.MERGE_NOSEQ)
+        np.testing.assert_array_equal(r["indices"], want)
