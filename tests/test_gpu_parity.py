@@ -166,23 +166,6 @@ def test_edge_values(ctx, oracle_mod):
         _check(ctx, oracle_mod, x, scheme, p, slices, rep="none", merge="sequential")
 
 
-def test_points_with_both_infinities(ctx, oracle_mod):
-    # a point holding +inf and -inf has no sum: both sides score it +inf, so
-    # it is ordered with the points it can dominate (those holding +inf in
-    # the same attribute), and the skyline, partitions and stage codes match
-    rng = np.random.default_rng(12)
-    x = rng.random((3000, 4)).astype(np.float32)
-    x[:200, 1] = np.inf
-    x[100:300, 3] = -np.inf          # 100 points hold both
-    x[300:400, 1] = np.inf
-    x[300:400, 2] = -np.inf          # both, in other attributes
-    x[500:700] = x[:200]             # duplicates of them
-    for scheme, p, sl in VARIANTS:
-        slices = [3, 3, 3, 3] if sl == "g" else ([3, 2, 2] if sl == "a" else None)
-        _check(ctx, oracle_mod, x, scheme, p, slices, rep="sorted", merge="noseq")
-        _check(ctx, oracle_mod, x, scheme, p, slices, rep="none", merge="sequential")
-
-
 def test_small_n(ctx, oracle_mod):
     for n in (1, 2, 3, 31, 32, 33, 63, 64, 65, 127, 129):
         x = datagen.independent(n, 4, n)
