@@ -651,3 +651,22 @@ def test_oracle_against_numpy_def1(oracle_mod, kind, d):
         r = oracle_mod.partitioned(pts, scheme=oracle_mod.SLICED, p=6, rep=oracle_mod.REP_SORTED,
                                    merge=oracle_mod.MERGE_NOSEQ)
         np.testing.assert_array_equal(r["indices"], want)
+
+
+def test_test_counters_hand_instance(oracle_mod):
+    # A = (1, 0.2), B = (2, 3), C = (3, 0.5), D = (4, 0.3); Sliced p = 2 on
+    # x_0 ranks them A, B, C, D, so partition 0 = {A, B}, partition 1 = {C, D}.
+    # Local SFS: partition 0 in score order A (1.2), B (5): B is tested once
+    # against A and dies (stage 4); partition 1: C (3.5), D (4.3): D is tested
+    # once against C and survives -- 2 local tests.  u = {A, C, D}.
+    # NoSeq (pd_1 = u_0 = {A}): A has no potential dominators; C and D are
+    # each tested once against A and die -- 2 tests.  The sequential final
+    # phase over u in score order: A, then C and D are each tested once
+    # against the window {A} and die -- 2 tests.  Sky = {A}.
+    x = np.array([[1.0, 0.2], [2.0, 3.0], [3.0, 0.5], [4.0, 0.3]], np.float32)
+    for merge in (oracle_mod.MERGE_NOSEQ, oracle_mod.MERGE_SEQUENTIAL):
+        r = oracle_mod.partitioned(x, scheme=oracle_mod.SLICED, p=2, merge=merge)
+        np.testing.assert_array_equal(r["pid"], [0, 0, 1, 1])
+        np.testing.assert_array_equal(r["stage"], [1, 4, 5, 5])
+        assert r["tests"] == [2, 2]
+        np.testing.assert_array_equal(r["indices"], [0])
